@@ -1,0 +1,174 @@
+/*
+ * gf2x.h -- multiplication of long bit-polynomials in GF(2)[x] on one GB300,
+ * by the Frobenius-partition additive FFT of Chen, Cheng, Kuo, Li and Yang,
+ * "Multiplying boolean Polynomials with Frobenius Partitions in Additive Fast
+ * Fourier Transform" (arXiv 1803.11301).
+ *
+ * Plain C ABI.  No CUDA, torch or C++ types appear in the signatures: device
+ * buffers are passed as plain pointers, streams as `void *` holding a
+ * cudaStream_t (NULL = the legacy default stream).
+ *
+ * Data layout (every entry point)
+ *   A bit-polynomial of `nbits` bits is ceil(nbits/64) little-endian uint64
+ *   words: bit t of word w is the coefficient of x^(64 w + t).  A vector of
+ *   GF(2^64) elements is one uint64 per element, in polynomial form modulo
+ *   x^64 + x^4 + x^3 + x + 1 (Sec. 4.3).
+ *
+ * Sizes (Alg. 5; m = 64, l_m = 6)
+ *   nc = na + nb - 1 bits (0 if na or nb is 0) is the product length;
+ *   n  = max(64, next power of two >= nc) is the transform length in bits;
+ *   l  = log2(n) - 6, n_p = 2^l = n/64 is the number of GF(2^64) points;
+ *   alpha = v_{l+32} (Eq. 6), the partition is Sigma = alpha + V_l.
+ *   n <= 2^37 (Sec. 3.1 length limit with m = 64), else GF2X_ETOOBIG.
+ *
+ * Ownership: every data pointer belongs to the caller and must stay valid
+ * until the stream has finished the work.  A context owns only its constant
+ * tables.  No entry point allocates device memory except gf2x_ctx_create.
+ * Calls are asynchronous (enqueue only) unless stated otherwise.
+ *
+ * Errors: argument errors are returned at once and nothing is enqueued.
+ * A CUDA launch error is returned as GF2X_ECUDA.  There is no CPU fallback:
+ * without a usable device, gf2x_ctx_create returns GF2X_ENODEV.
+ */
+#ifndef GF2X_GB300_H
+#define GF2X_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GF2X_API __attribute__((visibility("default")))
+#else
+#define GF2X_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF2X_OK = 0,
+    GF2X_EINVAL = 1,     /* null/misaligned pointer, overlap, bad size */
+    GF2X_ETOOBIG = 2,    /* transform length n above 2^37 bits */
+    GF2X_ENOMEM = 3,     /* device allocation failed (context creation only) */
+    GF2X_ECUDA = 4,      /* a CUDA call or launch failed */
+    GF2X_ETIMEOUT = 5,   /* a bounded device-side wait expired */
+    GF2X_ENODEV = 6,     /* no usable CUDA device */
+    GF2X_ENOSPACE = 7    /* workspace smaller than gf2x_workspace_bytes() */
+} gf2x_status;
+
+typedef struct gf2x_ctx gf2x_ctx;
+
+/* Human-readable name of a status code (static string). */
+GF2X_API const char *gf2x_status_string(gf2x_status s);
+
+/* Create a context on CUDA device `device`: computes the Cantor basis
+ * (Eq. 2), the Encode matrix and its inverse (Alg. 4, Prop. 2) and the
+ * twiddle tables on the host and uploads them.  Synchronous.  The current
+ * device of the calling thread is restored on return. */
+GF2X_API gf2x_status gf2x_ctx_create(gf2x_ctx **ctx, int device);
+
+/* Free a context (NULL is ignored).  Work enqueued with it must be done. */
+GF2X_API void gf2x_ctx_destroy(gf2x_ctx *ctx);
+
+/* Transform length n in bits for operands of na and nb bits (see above);
+ * 0 when na or nb is 0. */
+GF2X_API uint64_t gf2x_transform_bits(uint64_t na_bits, uint64_t nb_bits);
+
+/* Device workspace in bytes that gf2x_mul needs for these operand lengths
+ * (three buffers of n/8 bytes, 256-byte aligned). */
+GF2X_API size_t gf2x_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
+
+/* c = a * b in GF(2)[x]: FP_Polymul, Alg. 5 (Sec. 3.4), on `stream`.
+ *   a, b       device, ceil(na/64) and ceil(nb/64) words; bits at or above
+ *              na (nb) in the last word are ignored.  a == b is allowed.
+ *   c          device, ceil(nc/64) words; bits at or above nc are written 0.
+ *              c must not overlap a, b or the workspace.
+ *   workspace  device, >= gf2x_workspace_bytes(na, nb) bytes, 256-aligned;
+ *              contents on entry are ignored, on exit undefined.
+ * All device pointers 8-byte aligned.  na == 0 or nb == 0 is valid and
+ * writes nothing. */
+GF2X_API gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
+                     const uint64_t *b, uint64_t nb_bits, uint64_t *c,
+                     void *workspace, size_t ws_bytes, void *stream);
+
+/* The same product with HOST operands and result: copies a and b into the
+ * device workspace, runs gf2x_mul, copies c back and waits for the stream.
+ * Synchronous.  Host buffers may be pageable; pinned memory is faster.
+ * The workspace must hold gf2x_host_workspace_bytes(na, nb) bytes. */
+GF2X_API size_t gf2x_host_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
+GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na_bits,
+                          const uint64_t *b_host, uint64_t nb_bits, uint64_t *c_host,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+/* Read, and reset to GF2X_OK, the context's device status word after the
+ * work already enqueued on `stream` has finished (synchronises the stream).
+ * Device code records bounded-wait expiry (GF2X_ETIMEOUT) there; it never
+ * traps. */
+GF2X_API gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Per-stage profiling.  Stage k (0 <= k < gf2x_stage_count()) is one step of
+ * Alg. 5 as named by gf2x_stage_name(k): load, basis_cvt, encode, butterfly,
+ * pointwise, ibutterfly, decode, ibasis_cvt, store.
+ * ---------------------------------------------------------------------- */
+GF2X_API int gf2x_stage_count(void);
+GF2X_API const char *gf2x_stage_name(int stage);
+
+/* Reset the per-stage times and kernel-launch counters; with enable != 0,
+ * also bracket every later stage with a pair of CUDA events recorded on the
+ * stream that stage's kernels are launched on.  Launches are counted
+ * whether or not timing is enabled.  Synchronises with events already
+ * recorded. */
+GF2X_API gf2x_status gf2x_profile_enable(gf2x_ctx *ctx, int enable);
+
+/* Sum the recorded stage times (milliseconds) into ms[k] and copy the kernel
+ * launch counts into launches[k], k < min(max_stages, stage count).  Waits
+ * for the recorded events.  Either pointer may be NULL.  Returns the number
+ * of stages, or -1 for a NULL context. */
+GF2X_API int gf2x_profile_read(gf2x_ctx *ctx, double *ms, uint64_t *launches, int max_stages);
+
+/* ------------------------------------------------------------------------
+ * Stages of Alg. 5, exposed one by one (device pointers, enqueue only).
+ * They compute exactly what gf2x_mul computes internally and exist so that
+ * each step can be checked on its own.
+ * ---------------------------------------------------------------------- */
+
+/* BasisCvt, Alg. 1 (Sec. 2.3.1): monomial -> novelpoly basis, in place on
+ * the first L bits of `bits` (L a power of two, 64 <= L <= 2^37).  Bit k of
+ * the result is the coefficient of X_k.  Only XORs; GF(2)-linear. */
+GF2X_API gf2x_status gf2x_basis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L_bits, void *stream);
+
+/* iBasisCvt: the inverse map (novelpoly -> monomial), in place. */
+GF2X_API gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L_bits, void *stream);
+
+/* Encode, Alg. 4 (Sec. 3.3): f_i = sum_j a_{j n_p + i} r_j for i < n_p, with
+ * r_j = prod_t s_{l+t}(alpha)^{j_t} (the first l_m truncated butterfly
+ * layers; see Sec. 3.2).  `novel` holds n bits (n/64 words); f receives n_p
+ * elements.  No overlap allowed. */
+GF2X_API gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n_bits,
+                        uint64_t *f, void *stream);
+
+/* Decode: the inverse of Encode (uses R^{-1}, Prop. 2): n_p elements ->
+ * n bits.  No overlap allowed. */
+GF2X_API gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n_bits,
+                        uint64_t *novel, void *stream);
+
+/* Butterfly, Alg. 2 (Sec. 2.3.2) at alpha = v_{l+32}, in place on n_p
+ * elements: output k is f(alpha + u_k), u_k the element with Cantor
+ * coordinates k. */
+GF2X_API gf2x_status gf2x_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits, void *stream);
+
+/* iButterfly: the inverse of gf2x_butterfly, in place. */
+GF2X_API gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits, void *stream);
+
+/* Pointwise product in GF(2^64) (Alg. 5 line 7): c[i] = a[i] * b[i],
+ * i < count.  c may alias a or b. */
+GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b,
+                           uint64_t *c, uint64_t count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF2X_GB300_H */

@@ -30,10 +30,9 @@
 typedef uint64_t u64;
 
 /* ------------------------------------------------------------------ clmul */
-void oracle_clmul64(u64 a, u64 b, u64 *lo, u64 *hi)
+/* tab[t] = a * t for every 4-bit t, as a 67-bit value (tl[t], th[t]) */
+static void clmul_table(u64 a, u64 tl[16], u64 th[16])
 {
-    /* tab[t] = a * t for every 4-bit t, as a 67-bit value (tl, th) */
-    u64 tl[16], th[16];
     for (int t = 0; t < 16; ++t) {
         u64 l = 0, h = 0;
         for (int k = 0; k < 4; ++k)
@@ -44,8 +43,13 @@ void oracle_clmul64(u64 a, u64 b, u64 *lo, u64 *hi)
         tl[t] = l;
         th[t] = h;
     }
+}
+
+/* a * b from a's table: Horner over the nibbles of b, top nibble first */
+static void clmul_with_table(const u64 tl[16], const u64 th[16], u64 b, u64 *lo, u64 *hi)
+{
     u64 rl = 0, rh = 0;
-    for (int s = 60; s >= 0; s -= 4) {   /* Horner over the nibbles of b */
+    for (int s = 60; s >= 0; s -= 4) {
         rh = (rh << 4) | (rl >> 60);
         rl <<= 4;
         unsigned t = (unsigned)(b >> s) & 15u;
@@ -56,19 +60,29 @@ void oracle_clmul64(u64 a, u64 b, u64 *lo, u64 *hi)
     *hi = rh;
 }
 
+void oracle_clmul64(u64 a, u64 b, u64 *lo, u64 *hi)
+{
+    u64 tl[16], th[16];
+    clmul_table(a, tl, th);
+    clmul_with_table(tl, th, b, lo, hi);
+}
+
 /* c[0 .. na+nb) ^= a[0..na) * b[0..nb), word schoolbook */
 static void school(const u64 *a, size_t na, const u64 *b, size_t nb, u64 *c)
 {
-    for (size_t i = 0; i < na; ++i)
+    for (size_t i = 0; i < na; ++i) {
+        u64 tl[16], th[16];
+        clmul_table(a[i], tl, th);
         for (size_t j = 0; j < nb; ++j) {
             u64 lo, hi;
-            oracle_clmul64(a[i], b[j], &lo, &hi);
+            clmul_with_table(tl, th, b[j], &lo, &hi);
             c[i + j] ^= lo;
             c[i + j + 1] ^= hi;
         }
+    }
 }
 
-#define KARA_BASE 16
+#define KARA_BASE 32
 #define KARA_TASK_MIN 4096
 
 /* c[0..2n) = a[0..n) * b[0..n), n a power of two; ws holds >= 4n words. */

@@ -385,3 +385,43 @@ def fp_polymul(a: int, na: int, b: int, nb: int) -> int:
     h = ibutterfly(chat, tw)                          # line 8
     C_novel = decode(h, n)                            # line 9
     return ibasis_cvt(C_novel, n)                     # line 10
+
+
+# ------------------------------------------------ novelpoly evaluation (Def.)
+def novelpoly_eval(g_words: np.ndarray, L: int, beta: int) -> int:
+    """sum_k g_k X_k(beta) for the novelpoly coefficient bits g (uint64 words).
+
+    X_k = prod_{bits b of k} s_b (Def. of novelpoly).  Write k = 256 q + t
+    (t < 256): X_k = X_{256 q} X_t, so the sum is
+    sum_q X_{256 q}(beta) * (sum_t g_{256 q + t} X_t(beta)).  The inner sums
+    are XORs of the 256 values X_t(beta); the outer sum splits on the top bit
+    of q: G(v) = G(v_lo) + s_b(beta) * G(v_hi), folded from the top bit down.
+    """
+    K = log2_exact(L)
+    lo = min(K, 8)
+    sb = [F.s_eval(b, beta) for b in range(K)]
+    X = [1] * (1 << lo)
+    for t in range(1, 1 << lo):
+        low = (t & -t).bit_length() - 1
+        X[t] = F.gf_mul(X[t & (t - 1)], sb[low])
+    w = np.asarray(g_words, dtype=np.uint64)[: max(L // 64, 1)]
+    raw = w.view(np.uint8)
+    if L < 64:
+        raw = np.unpackbits(raw, bitorder="little")[:L]
+        raw = np.packbits(np.pad(raw, (0, 8 - L % 8 if L % 8 else 0)), bitorder="little")
+    nbytes = max((1 << lo) // 8, 1)
+    blocks = raw[: (L + 7) // 8].reshape(-1, nbytes)
+    vals = np.zeros(blocks.shape[0], dtype=np.uint64)
+    for p in range(nbytes):
+        tab = np.zeros(256, dtype=np.uint64)
+        for v in range(256):
+            acc = 0
+            for b in range(8):
+                if (v >> b) & 1 and 8 * p + b < len(X):
+                    acc ^= X[8 * p + b]
+            tab[v] = acc
+        vals ^= tab[blocks[:, p]]
+    for b in range(K - 1, lo - 1, -1):
+        half = len(vals) // 2
+        vals = vals[:half] ^ F.gf_mul_arr(vals[half:], sb[b])
+    return int(vals[0])

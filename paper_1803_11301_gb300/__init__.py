@@ -1,0 +1,256 @@
+"""GF(2)[x] multiplication on GB300 by the Frobenius-partition additive FFT.
+
+Thin Python binding over the C ABI in ``include/gf2x.h`` (library
+``_build/libgf2x_gb300.so``).  This module only marshals arguments: every
+step of the computation runs in the CUDA kernels behind the ABI.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the
+library is missing or no GPU is usable, the calls raise.
+
+Operands are packed bit-polynomials: ceil(nbits/64) 64-bit words (torch
+int64 or uint64 tensors, bit patterns), bit t of word w = coefficient of
+x^(64 w + t).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB as LIB_PATH
+
+__all__ = ["Context", "Gf2xError", "load_library", "transform_bits", "workspace_bytes",
+           "host_workspace_bytes", "product_bits", "ABI_FUNCTIONS", "STATUS"]
+
+STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
+          5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE"}
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+_ST = ctypes.c_int
+
+# name -> (restype, argtypes); the functions declared in include/gf2x.h
+ABI_FUNCTIONS = {
+    "gf2x_status_string": (ctypes.c_char_p, [_ST]),
+    "gf2x_ctx_create": (_ST, [ctypes.POINTER(_P), ctypes.c_int]),
+    "gf2x_ctx_destroy": (None, [_P]),
+    "gf2x_transform_bits": (_U64, [_U64, _U64]),
+    "gf2x_workspace_bytes": (_SZ, [_U64, _U64]),
+    "gf2x_mul": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
+    "gf2x_host_workspace_bytes": (_SZ, [_U64, _U64]),
+    "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
+    "gf2x_stream_status": (_ST, [_P, _P]),
+    "gf2x_basis_cvt": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_ibasis_cvt": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_encode": (_ST, [_P, _P, _U64, _P, _P]),
+    "gf2x_decode": (_ST, [_P, _P, _U64, _P, _P]),
+    "gf2x_butterfly": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_ibutterfly": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
+    "gf2x_stage_count": (ctypes.c_int, []),
+    "gf2x_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "gf2x_profile_enable": (_ST, [_P, ctypes.c_int]),
+    "gf2x_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64), ctypes.c_int]),
+}
+
+_lib = None
+
+
+class Gf2xError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libgf2x_gb300.so (built by ``paper_1803_11301_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1803_11301_gb300.build` "
+                              "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in ABI_FUNCTIONS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise Gf2xError(status, what)
+
+
+def product_bits(na: int, nb: int) -> int:
+    return na + nb - 1 if (na and nb) else 0
+
+
+def transform_bits(na: int, nb: int) -> int:
+    return int(load_library().gf2x_transform_bits(na, nb))
+
+
+def workspace_bytes(na: int, nb: int) -> int:
+    return int(load_library().gf2x_workspace_bytes(na, nb))
+
+
+def host_workspace_bytes(na: int, nb: int) -> int:
+    return int(load_library().gf2x_host_workspace_bytes(na, nb))
+
+
+def _words(nbits: int) -> int:
+    return (nbits + 63) // 64
+
+
+class Context:
+    """A gf2x context on one CUDA device (constant tables resident in HBM)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self._lib.gf2x_ctx_create(ctypes.byref(h), device), "gf2x_ctx_create")
+        self._h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gf2x_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def _stream(self, stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.device)
+
+    def _tensor_ptr(self, t, min_words: int, name: str):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous int64/uint64 tensor of words")
+        if t.numel() < min_words:
+            raise ValueError(f"{name} has {t.numel()} words, needs {min_words}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty_words(self, count: int):
+        import torch
+        return torch.empty(max(count, 1), dtype=torch.int64, device=self._dev())[:count]
+
+    def workspace(self, nbytes: int):
+        """A cached device workspace of at least nbytes (256-byte aligned)."""
+        import torch
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self._dev())
+            if self._ws.data_ptr() % 256:
+                raise RuntimeError("workspace allocation is not 256-byte aligned")
+        return self._ws
+
+    # --------------------------------------------------------- the product
+    def mul(self, a, na: int, b, nb: int, out=None, workspace=None, stream=None):
+        """c = a * b (Alg. 5) on the GPU; returns the ceil(nc/64)-word tensor c."""
+        nc = product_bits(na, nb)
+        if out is None:
+            out = self.empty_words(_words(nc))
+        if nc == 0:
+            return out
+        need = workspace_bytes(na, nb)
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_mul(self._h, self._tensor_ptr(a, _words(na), "a"), na,
+                                  self._tensor_ptr(b, _words(nb), "b"), nb,
+                                  self._tensor_ptr(out, _words(nc), "out"),
+                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                  self._stream(stream)), "gf2x_mul")
+        return out
+
+    def mul_host(self, a, na: int, b, nb: int, out=None, workspace=None, stream=None):
+        """The product with host (numpy uint64) operands and result, through gf2x_mul_host."""
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        nc = product_bits(na, nb)
+        if out is None:
+            out = np.zeros(_words(nc), dtype=np.uint64)
+        if nc == 0:
+            return out
+        if a.size < _words(na) or b.size < _words(nb) or out.size < _words(nc):
+            raise ValueError("host buffer too small")
+        need = host_workspace_bytes(na, nb)
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_mul_host(self._h, ctypes.c_void_p(a.ctypes.data), na,
+                                       ctypes.c_void_p(b.ctypes.data), nb, ctypes.c_void_p(out.ctypes.data),
+                                       ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                       self._stream(stream)), "gf2x_mul_host")
+        return out
+
+    def profile_enable(self, enable: bool = True):
+        """Reset stage times and launch counts; time every later stage with CUDA events if enable."""
+        _check(self._lib.gf2x_profile_enable(self._h, 1 if enable else 0), "gf2x_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage name: (milliseconds, kernel launches)} accumulated since profile_enable."""
+        n = self._lib.gf2x_stage_count()
+        ms = (ctypes.c_double * n)()
+        la = (_U64 * n)()
+        self._lib.gf2x_profile_read(self._h, ms, la, n)
+        return {self._lib.gf2x_stage_name(k).decode(): (ms[k], int(la[k])) for k in range(n)}
+
+    def stream_status(self, stream=None) -> int:
+        return int(self._lib.gf2x_stream_status(self._h, self._stream(stream)))
+
+    # -------------------------------------------------------------- stages
+    def basis_cvt(self, bits, L: int, stream=None, inverse: bool = False):
+        fn = self._lib.gf2x_ibasis_cvt if inverse else self._lib.gf2x_basis_cvt
+        _check(fn(self._h, self._tensor_ptr(bits, L // 64, "bits"), L, self._stream(stream)),
+               "gf2x_ibasis_cvt" if inverse else "gf2x_basis_cvt")
+        return bits
+
+    def ibasis_cvt(self, bits, L: int, stream=None):
+        return self.basis_cvt(bits, L, stream, inverse=True)
+
+    def encode(self, novel, n: int, out=None, stream=None):
+        if out is None:
+            out = self.empty_words(n // 64)
+        _check(self._lib.gf2x_encode(self._h, self._tensor_ptr(novel, n // 64, "novel"), n,
+                                     self._tensor_ptr(out, n // 64, "out"), self._stream(stream)), "gf2x_encode")
+        return out
+
+    def decode(self, h, n: int, out=None, stream=None):
+        if out is None:
+            out = self.empty_words(n // 64)
+        _check(self._lib.gf2x_decode(self._h, self._tensor_ptr(h, n // 64, "h"), n,
+                                     self._tensor_ptr(out, n // 64, "out"), self._stream(stream)), "gf2x_decode")
+        return out
+
+    def butterfly(self, f, n: int, stream=None, inverse: bool = False):
+        fn = self._lib.gf2x_ibutterfly if inverse else self._lib.gf2x_butterfly
+        _check(fn(self._h, self._tensor_ptr(f, n // 64, "f"), n, self._stream(stream)),
+               "gf2x_ibutterfly" if inverse else "gf2x_butterfly")
+        return f
+
+    def ibutterfly(self, f, n: int, stream=None):
+        return self.butterfly(f, n, stream, inverse=True)
+
+    def pointwise(self, a, b, out=None, stream=None):
+        count = a.numel()
+        if out is None:
+            out = self.empty_words(count)
+        _check(self._lib.gf2x_pointwise(self._h, self._tensor_ptr(a, count, "a"), self._tensor_ptr(b, count, "b"),
+                                        self._tensor_ptr(out, count, "out"), count, self._stream(stream)),
+               "gf2x_pointwise")
+        return out

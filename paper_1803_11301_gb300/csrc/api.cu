@@ -1,0 +1,545 @@
+// C ABI of the GB300 GF(2)[x] multiplier (declared in include/gf2x.h) and
+// the host-side set-up: Cantor basis, Encode matrix R and its inverse,
+// Cantor-to-polynomial table.
+//
+// FP_Polymul (Alg. 5) on one stream, three workspace buffers X, Y, T of n/64
+// words each:
+//   T <- a (masked, zero-padded to n bits); BasisCvt(T, L_a); X <- Encode(T);
+//   Butterfly(X)                                                 (lines 1-3)
+//   T <- b ...; Y <- Encode(T); Butterfly(Y)                     (lines 4-6)
+//   X <- X * Y pointwise                                         (line 7)
+//   iButterfly(X); T <- Decode(X); iBasisCvt(T, n); c <- T        (lines 8-10)
+// BasisCvt runs on L_a = max(64, next_pow2(na)) bits: the novelpoly basis
+// is triangular (deg X_k = k), so the coefficients at k >= L_a are zero.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gf2x_common.cuh"
+
+namespace {
+
+constexpr u64 kMaxTransformBits = 1ull << 37;    // Sec. 3.1 length limit, m = 64
+constexpr size_t kAlign = 256;
+
+// ------------------------------------------------------------ host GF(2^64)
+u64 hmul(u64 a, u64 b)
+{
+    u64 r = 0;
+    for (int t = 0; t < 64; ++t) {
+        if ((b >> t) & 1) r ^= a;
+        a = (a << 1) ^ ((a >> 63) ? GF2X_MOD_LOW : 0);
+    }
+    return r;
+}
+
+// Solve sum_k y_k img[k] = rhs over GF(2); one solution or false.
+bool gf2_solve(const u64 img[64], u64 rhs, u64 *y)
+{
+    u64 eq[64];          // equation for bit position p: coefficient mask over k
+    int rhsb[64];
+    for (int p = 0; p < 64; ++p) {
+        u64 m = 0;
+        for (int k = 0; k < 64; ++k) m |= ((img[k] >> p) & 1ull) << k;
+        eq[p] = m;
+        rhsb[p] = (int)((rhs >> p) & 1);
+    }
+    int piv_col[64];
+    int rank = 0;
+    for (int col = 0; col < 64 && rank < 64; ++col) {
+        int piv = -1;
+        for (int r = rank; r < 64; ++r)
+            if ((eq[r] >> col) & 1) { piv = r; break; }
+        if (piv < 0) continue;
+        std::swap(eq[rank], eq[piv]);
+        std::swap(rhsb[rank], rhsb[piv]);
+        for (int r = 0; r < 64; ++r)
+            if (r != rank && ((eq[r] >> col) & 1)) { eq[r] ^= eq[rank]; rhsb[r] ^= rhsb[rank]; }
+        piv_col[rank++] = col;
+    }
+    for (int r = rank; r < 64; ++r)
+        if (rhsb[r]) return false;
+    u64 sol = 0;
+    for (int r = 0; r < rank; ++r)
+        if (rhsb[r]) sol |= 1ull << piv_col[r];
+    *y = sol;
+    return true;
+}
+
+// rows of A^{-1} for the 64x64 GF(2) matrix with rows a[] (row-vector convention)
+bool gf2_inverse(const u64 a_in[64], u64 inv[64])
+{
+    u64 a[64];
+    for (int k = 0; k < 64; ++k) { a[k] = a_in[k]; inv[k] = 1ull << k; }
+    for (int col = 0; col < 64; ++col) {
+        int piv = -1;
+        for (int r = col; r < 64; ++r)
+            if ((a[r] >> col) & 1) { piv = r; break; }
+        if (piv < 0) return false;
+        std::swap(a[col], a[piv]);
+        std::swap(inv[col], inv[piv]);
+        for (int r = 0; r < 64; ++r)
+            if (r != col && ((a[r] >> col) & 1)) { a[r] ^= a[col]; inv[r] ^= inv[col]; }
+    }
+    return true;
+}
+
+// v_0 = 1, v_i^2 + v_i = v_{i-1} (Eq. 2); of the two roots y, y + 1 take the
+// one with bit 0 clear.
+bool cantor_basis(u64 v[64])
+{
+    u64 img[64];
+    for (int k = 0; k < 64; ++k) {
+        u64 e = 1ull << k;
+        img[k] = hmul(e, e) ^ e;
+    }
+    v[0] = 1;
+    for (int i = 1; i < 64; ++i) {
+        u64 y;
+        if (!gf2_solve(img, v[i - 1], &y)) return false;
+        v[i] = y & ~1ull;
+    }
+    return true;
+}
+
+void window_table(const u64 rows[64], u64 *tab)
+{
+    for (int k = 0; k < 8; ++k)
+        for (int x = 0; x < 256; ++x) {
+            u64 r = 0;
+            for (int b = 0; b < 8; ++b)
+                if ((x >> b) & 1) r ^= rows[8 * k + b];
+            tab[k * 256 + x] = r;
+        }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+u64 next_pow2(u64 x)
+{
+    u64 p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int log2_u64(u64 x)
+{
+    int k = 0;
+    while ((1ull << k) < x) ++k;
+    return k;
+}
+
+size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
+
+bool overlap(const void *p, size_t pb, const void *q, size_t qb)
+{
+    uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+    return pb && qb && a < b + qb && b < a + pb;
+}
+
+gf2x_status from_cuda(cudaError_t e) { return e == cudaSuccess ? GF2X_OK : GF2X_ECUDA; }
+
+#define TRY(expr)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return GF2X_ECUDA;                 \
+    } while (0)
+
+u64 product_bits(u64 na, u64 nb) { return (na && nb) ? na + nb - 1 : 0; }
+
+u64 transform_bits(u64 na, u64 nb)
+{
+    u64 nc = product_bits(na, nb);
+    if (!nc) return 0;
+    u64 n = next_pow2(nc);
+    return n < 64 ? 64 : n;
+}
+
+size_t buffer_bytes(u64 n) { return round_up((size_t)(n / 8)); }
+
+// ------------------------------------------------------------- profiling
+// Optional per-stage timing: a pair of CUDA events around every stage,
+// recorded on the stream the stage's kernels are launched on.  Read back (and
+// summed per stage) by gf2x_profile_read.
+struct Profiler {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> stage_of;          // per event pair
+    size_t used = 0;                    // events recorded since the last read
+    double ms[STAGE_COUNT] = {};
+};
+
+Profiler *profiler(gf2x_ctx *ctx) { return (Profiler *)ctx->prof; }
+
+void stage_begin(gf2x_ctx *ctx, int stage, cudaStream_t st)
+{
+    ctx->stage = stage;
+    if (!ctx->profiling) return;
+    Profiler *p = profiler(ctx);
+    while (p->ev.size() < p->used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p->ev.push_back(e);
+    }
+    p->stage_of.resize(p->ev.size() / 2 + 1);
+    p->stage_of[p->used / 2] = stage;
+    cudaEventRecord(p->ev[p->used], st);
+}
+
+void stage_end(gf2x_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx->profiling) return;
+    Profiler *p = profiler(ctx);
+    if (p->ev.size() < p->used + 2) return;
+    cudaEventRecord(p->ev[p->used + 1], st);
+    p->used += 2;
+}
+
+struct StageScope {
+    gf2x_ctx *ctx;
+    cudaStream_t st;
+    StageScope(gf2x_ctx *c, int stage, cudaStream_t s) : ctx(c), st(s) { stage_begin(c, stage, s); }
+    ~StageScope() { stage_end(ctx, st); }
+};
+
+// The forward half of Alg. 5 for one operand: lines 1-3 (or 4-6).
+gf2x_status forward(gf2x_ctx *ctx, const u64 *src, u64 nsrc, u64 n, u64 *T, u64 *F, cudaStream_t st)
+{
+    const int l = log2_u64(n) - 6;
+    u64 L = next_pow2(nsrc);
+    if (L < 64) L = 64;
+    { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, src, nsrc, T, n / 64, st)); }
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, st)); }
+    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, F, st)); }
+    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, F, l, false, st)); }
+    return GF2X_OK;
+}
+
+gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                       cudaStream_t st)
+{
+    const u64 n = transform_bits(na, nb), nc = product_bits(na, nb);
+    const int l = log2_u64(n) - 6;
+    const size_t buf = buffer_bytes(n);
+    u64 *X = (u64 *)ws;
+    u64 *Y = (u64 *)((char *)ws + buf);
+    u64 *T = (u64 *)((char *)ws + 2 * buf);
+    gf2x_status s = forward(ctx, a, na, n, T, X, st);
+    if (s != GF2X_OK) return s;
+    const bool square = (a == b && na == nb);
+    if (!square) {
+        s = forward(ctx, b, nb, n, T, Y, st);
+        if (s != GF2X_OK) return s;
+    }
+    { StageScope s(ctx, STAGE_POINTWISE, st); TRY(gf2x::pointwise(ctx, X, square ? X : Y, X, n / 64, st)); }
+    { StageScope s(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly(ctx, X, l, true, st)); }
+    { StageScope s(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, T, st)); }
+    { StageScope s(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, st)); }
+    { StageScope s(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, nc, c, st)); }
+    return GF2X_OK;
+}
+
+bool valid_n(u64 n) { return n >= 64 && n <= kMaxTransformBits && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *gf2x_status_string(gf2x_status s)
+{
+    switch (s) {
+    case GF2X_OK: return "GF2X_OK";
+    case GF2X_EINVAL: return "GF2X_EINVAL";
+    case GF2X_ETOOBIG: return "GF2X_ETOOBIG";
+    case GF2X_ENOMEM: return "GF2X_ENOMEM";
+    case GF2X_ECUDA: return "GF2X_ECUDA";
+    case GF2X_ETIMEOUT: return "GF2X_ETIMEOUT";
+    case GF2X_ENODEV: return "GF2X_ENODEV";
+    case GF2X_ENOSPACE: return "GF2X_ENOSPACE";
+    }
+    return "GF2X_UNKNOWN";
+}
+
+gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
+{
+    if (!out) return GF2X_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) return GF2X_ENODEV;
+    if (device < 0 || device >= count) return GF2X_ENODEV;
+    DeviceGuard g(device);
+    if (!g.ok) return GF2X_ENODEV;
+
+    gf2x_ctx *ctx = new (std::nothrow) gf2x_ctx();
+    if (!ctx) return GF2X_ENOMEM;
+    ctx->device = device;
+    ctx->prof = new (std::nothrow) Profiler();
+    if (!ctx->prof) { delete ctx; return GF2X_ENOMEM; }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+
+    u64 v[64];
+    auto fail = [&](gf2x_status st) { delete profiler(ctx); delete ctx; return st; };
+    if (!cantor_basis(v)) return fail(GF2X_EINVAL);
+    std::memcpy(ctx->cantor, v, sizeof v);
+
+    // Encode multipliers: layer l+t of the truncated Butterfly multiplies by
+    // s_{l+t}(v_{l+32}) = v_{32-t} (Eq. 4), the same for every l; row j of R
+    // is r_j = prod_{t: bit t of j} v_{32-t} (Alg. 4, Sec. 3.3).
+    u64 r[64], rinv[64];
+    for (int j = 0; j < 64; ++j) {
+        u64 p = 1;
+        for (int t = 0; t < 6; ++t)
+            if ((j >> t) & 1) p = hmul(p, v[32 - t]);
+        r[j] = p;
+    }
+    if (!gf2_inverse(r, rinv)) return fail(GF2X_EINVAL);   // Prop. 2
+
+    std::vector<u64> host(3 * 2048 + 64);
+    window_table(v, &host[0]);
+    window_table(r, &host[2048]);
+    window_table(rinv, &host[4096]);
+    std::memcpy(&host[6144], v, sizeof v);
+
+    if (cudaMalloc(&ctx->d_tables, host.size() * sizeof(u64)) != cudaSuccess) return fail(GF2X_ENOMEM);
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->d_tables);
+        return fail(GF2X_ENOMEM);
+    }
+    ctx->d_cvt = ctx->d_tables;
+    ctx->d_enc = ctx->d_tables + 2048;
+    ctx->d_dec = ctx->d_tables + 4096;
+    ctx->d_cantor = ctx->d_tables + 6144;
+    if (cudaMemcpy(ctx->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->d_tables);
+        cudaFree(ctx->d_status);
+        return fail(GF2X_ECUDA);
+    }
+    *out = ctx;
+    return GF2X_OK;
+}
+
+void gf2x_ctx_destroy(gf2x_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (Profiler *p = profiler(ctx)) {
+        for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+        delete p;
+    }
+    cudaFree(ctx->d_tables);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+uint64_t gf2x_transform_bits(uint64_t na, uint64_t nb) { return transform_bits(na, nb); }
+
+size_t gf2x_workspace_bytes(uint64_t na, uint64_t nb)
+{
+    u64 n = transform_bits(na, nb);
+    if (!n || n > kMaxTransformBits) return 0;
+    return 3 * buffer_bytes(n);
+}
+
+gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *c,
+                     void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    const u64 nc = product_bits(na, nb);
+    if (!nc) return GF2X_OK;
+    const u64 n = transform_bits(na, nb);
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!a || !b || !c || !ws || !aligned8(a) || !aligned8(b) || !aligned8(c) || ((uintptr_t)ws % kAlign))
+        return GF2X_EINVAL;
+    const size_t need = gf2x_workspace_bytes(na, nb);
+    if (ws_bytes < need) return GF2X_ENOSPACE;
+    const size_t cb = (size_t)((nc + 63) / 64) * 8;
+    if (overlap(c, cb, a, (size_t)((na + 63) / 64) * 8) || overlap(c, cb, b, (size_t)((nb + 63) / 64) * 8) ||
+        overlap(c, cb, ws, need))
+        return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    return mul_device(ctx, a, na, b, nb, c, ws, (cudaStream_t)stream);
+}
+
+size_t gf2x_host_workspace_bytes(uint64_t na, uint64_t nb)
+{
+    size_t base = gf2x_workspace_bytes(na, nb);
+    if (!base) return 0;
+    u64 nc = product_bits(na, nb);
+    return base + round_up((size_t)((na + 63) / 64) * 8) + round_up((size_t)((nb + 63) / 64) * 8) +
+           round_up((size_t)((nc + 63) / 64) * 8);
+}
+
+gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, const uint64_t *b_host, uint64_t nb,
+                          uint64_t *c_host, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    const u64 nc = product_bits(na, nb);
+    if (!nc) return GF2X_OK;
+    if (transform_bits(na, nb) > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!a_host || !b_host || !c_host || !ws || ((uintptr_t)ws % kAlign)) return GF2X_EINVAL;
+    const size_t need = gf2x_host_workspace_bytes(na, nb);
+    if (ws_bytes < need) return GF2X_ENOSPACE;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t base = gf2x_workspace_bytes(na, nb);
+    const size_t ab = (size_t)((na + 63) / 64) * 8, bb = (size_t)((nb + 63) / 64) * 8,
+                 cb = (size_t)((nc + 63) / 64) * 8;
+    u64 *da = (u64 *)((char *)ws + base);
+    u64 *db = (u64 *)((char *)da + round_up(ab));
+    u64 *dc = (u64 *)((char *)db + round_up(bb));
+    TRY(cudaMemcpyAsync(da, a_host, ab, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, st));
+    gf2x_status s = mul_device(ctx, da, na, db, nb, dc, ws, st);
+    if (s != GF2X_OK) return s;
+    TRY(cudaMemcpyAsync(c_host, dc, cb, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    return GF2X_OK;
+}
+
+gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    TRY(cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+        TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        TRY(cudaStreamSynchronize(st));
+    }
+    return (gf2x_status)h;
+}
+
+gf2x_status gf2x_basis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stream)
+{
+    if (!ctx || !bits || !aligned8(bits)) return GF2X_EINVAL;
+    if (L > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(L)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_BASISCVT, (cudaStream_t)stream);
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, false, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stream)
+{
+    if (!ctx || !bits || !aligned8(bits)) return GF2X_EINVAL;
+    if (L > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(L)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_IBASISCVT, (cudaStream_t)stream);
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, true, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64_t *f, void *stream)
+{
+    if (!ctx || !novel || !f || !aligned8(novel) || !aligned8(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
+    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)
+{
+    if (!ctx || !novel || !h || !aligned8(novel) || !aligned8(h)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(n) || overlap(novel, n / 8, h, n / 8)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_DECODE, (cudaStream_t)stream);
+    return from_cuda(gf2x::decode(ctx, h, log2_u64(n) - 6, novel, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
+{
+    if (!ctx || !f || !aligned8(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(n)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_BUTTERFLY, (cudaStream_t)stream);
+    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, false, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
+{
+    if (!ctx || !f || !aligned8(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(n)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_IBUTTERFLY, (cudaStream_t)stream);
+    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, true, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint64_t count,
+                           void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    if (!count) return GF2X_OK;
+    if (!a || !b || !c || !aligned8(a) || !aligned8(b) || !aligned8(c)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_POINTWISE, (cudaStream_t)stream);
+    return from_cuda(gf2x::pointwise(ctx, a, b, c, count, (cudaStream_t)stream));
+}
+
+const char *gf2x_stage_name(int stage)
+{
+    static const char *names[STAGE_COUNT] = {"load", "basis_cvt", "encode", "butterfly", "pointwise",
+                                             "ibutterfly", "decode", "ibasis_cvt", "store"};
+    return (stage >= 0 && stage < STAGE_COUNT) ? names[stage] : "unknown";
+}
+
+int gf2x_stage_count(void) { return STAGE_COUNT; }
+
+gf2x_status gf2x_profile_enable(gf2x_ctx *ctx, int enable)
+{
+    if (!ctx) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    Profiler *p = profiler(ctx);
+    if (p->used) cudaEventSynchronize(p->ev[p->used - 1]);
+    p->used = 0;
+    for (double &m : p->ms) m = 0;
+    for (auto &l : ctx->launches) l = 0;
+    ctx->profiling = enable != 0;
+    return GF2X_OK;
+}
+
+int gf2x_profile_read(gf2x_ctx *ctx, double *ms, uint64_t *launches, int max_stages)
+{
+    if (!ctx) return -1;
+    DeviceGuard g(ctx->device);
+    Profiler *p = profiler(ctx);
+    if (p->used) {
+        cudaEventSynchronize(p->ev[p->used - 1]);
+        for (size_t k = 0; k + 1 < p->used; k += 2) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, p->ev[k], p->ev[k + 1]) == cudaSuccess) p->ms[p->stage_of[k / 2]] += t;
+        }
+        p->used = 0;
+    }
+    int n = max_stages < STAGE_COUNT ? max_stages : STAGE_COUNT;
+    for (int k = 0; k < n; ++k) {
+        if (ms) ms[k] = p->ms[k];
+        if (launches) launches[k] = ctx->launches[k];
+    }
+    return STAGE_COUNT;
+}
+
+}  // extern "C"

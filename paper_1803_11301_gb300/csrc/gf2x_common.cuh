@@ -1,0 +1,108 @@
+// Shared definitions of the GB300 GF(2)[x] multiplier (device + host side).
+//
+// Field: GF(2^64) = GF(2)[x] / (x^64 + x^4 + x^3 + x + 1), polynomial form
+// (Sec. 4.3).  The GPU has no carry-less multiply instruction, so the product
+// is built from 32x32->64 integer multiplies on operands with "holes"
+// (every fourth bit kept, so no carry reaches a kept bit), Karatsuba over the
+// 32-bit halves, and a two-step fold of the high word by x^4 + x^3 + x + 1.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gf2x.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+#define GF2X_MOD_LOW 0x1Bull   // x^4 + x^3 + x + 1
+
+// ------------------------------------------------------------ field arithmetic
+// 32 x 32 -> 64-bit carry-less product.  a_i = a & (0x1111... << i) keeps one
+// bit in four; the integer product a_i * b_j has at most 8 terms per output
+// position, so each count fits in the 4-bit gap and its parity is the
+// carry-less bit.  Positions of class k (mod 4) come from the pairs i+j = k.
+__device__ __forceinline__ u64 clmul32(u32 a, u32 b)
+{
+    const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
+    u32 a0 = a & m0, a1 = a & m1, a2 = a & m2, a3 = a & m3;
+    u32 b0 = b & m0, b1 = b & m1, b2 = b & m2, b3 = b & m3;
+    u64 z0 = ((u64)a0 * b0) ^ ((u64)a1 * b3) ^ ((u64)a2 * b2) ^ ((u64)a3 * b1);
+    u64 z1 = ((u64)a0 * b1) ^ ((u64)a1 * b0) ^ ((u64)a2 * b3) ^ ((u64)a3 * b2);
+    u64 z2 = ((u64)a0 * b2) ^ ((u64)a1 * b1) ^ ((u64)a2 * b0) ^ ((u64)a3 * b3);
+    u64 z3 = ((u64)a0 * b3) ^ ((u64)a1 * b2) ^ ((u64)a2 * b1) ^ ((u64)a3 * b0);
+    return (z0 & 0x1111111111111111ull) | (z1 & 0x2222222222222222ull) |
+           (z2 & 0x4444444444444444ull) | (z3 & 0x8888888888888888ull);
+}
+
+// (hi, lo) -> hi * x^64 + lo reduced: x^64 = x^4 + x^3 + x + 1.
+__device__ __forceinline__ u64 gf64_reduce(u64 hi, u64 lo)
+{
+    u64 t = hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4);
+    u64 over = (hi >> 63) ^ (hi >> 61) ^ (hi >> 60);      // bits 64..67 of hi * 0x1B
+    t ^= over ^ (over << 1) ^ (over << 3) ^ (over << 4);
+    return lo ^ t;
+}
+
+__device__ __forceinline__ u64 gf64_mul(u64 a, u64 b)
+{
+    u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+    u64 lo = clmul32(al, bl);
+    u64 hi = clmul32(ah, bh);
+    u64 mid = clmul32(al ^ ah, bl ^ bh) ^ lo ^ hi;          // Karatsuba middle term
+    return gf64_reduce(hi ^ (mid >> 32), lo ^ (mid << 32));
+}
+
+// 64-bit GF(2)-linear map given as 8 byte-window tables (t[k][v] = image of
+// v << 8k): the method of four Russians with 8-bit windows (Sec. 4.5).
+__device__ __forceinline__ u64 lin64(const u64 *__restrict__ t, u64 x)
+{
+    u64 r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r ^= t[k * 256 + ((x >> (8 * k)) & 255)];
+    return r;
+}
+
+// ------------------------------------------------------------------ context
+// Stages of Alg. 5 as the profiler and the launch counter see them.
+enum Gf2xStage {
+    STAGE_LOAD = 0, STAGE_BASISCVT, STAGE_ENCODE, STAGE_BUTTERFLY, STAGE_POINTWISE,
+    STAGE_IBUTTERFLY, STAGE_DECODE, STAGE_IBASISCVT, STAGE_STORE, STAGE_COUNT
+};
+
+struct gf2x_ctx {
+    int device;
+    int num_sms;
+    u64 *d_tables;      // one allocation holding the tables below
+    u64 *d_cvt;         // 8 x 256: Cantor coordinates -> polynomial form
+    u64 *d_enc;         // 8 x 256: bits (a_{j n_p + i})_j -> f_i  (matrix R)
+    u64 *d_dec;         // 8 x 256: f_i -> bits                    (matrix R^{-1})
+    u64 *d_cantor;      // v_0 .. v_63
+    int *d_status;      // device status word (gf2x_status)
+    u64 cantor[64];     // host copy of the Cantor basis
+
+    // launch accounting and optional per-stage event timing (host side)
+    int stage;                          // stage the next launches belong to
+    unsigned long long launches[STAGE_COUNT];
+    bool profiling;
+    void *prof;                         // event pool, see api.cu
+};
+
+// Count one kernel launch against the current stage.
+inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] += (unsigned long long)n; }
+
+// ----------------------------------------------------------------- launchers
+// All enqueue on `st` and return cudaGetLastError().
+namespace gf2x {
+
+cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_t st);
+cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, cudaStream_t st);
+cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t st);
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st);
+cudaError_t pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
+cudaError_t load_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, u64 dst_words, cudaStream_t st);
+cudaError_t store_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, cudaStream_t st);
+
+}  // namespace gf2x

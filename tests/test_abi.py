@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every symbol include/gf2x.h declares (CPU only).
+
+No compute call is made here: these run without a GPU.  Only the pure host
+functions (size rules) and the no-device error path are exercised.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gf2x.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"GF2X_API\s+[\w\s\*]*?\b(gf2x_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_11301_gb300 import build, load_library
+    build.build()
+    return load_library()
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for must in ["gf2x_ctx_create", "gf2x_ctx_destroy", "gf2x_mul", "gf2x_workspace_bytes",
+                 "gf2x_stream_status", "gf2x_mul_host", "gf2x_basis_cvt", "gf2x_encode",
+                 "gf2x_butterfly", "gf2x_pointwise", "gf2x_decode", "gf2x_ibutterfly", "gf2x_ibasis_cvt"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1803_11301_gb300 import ABI_FUNCTIONS
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in ABI_FUNCTIONS, f"binding does not marshal {name}"
+
+
+def test_size_rules_match_the_oracle(lib):
+    from paper_1803_11301_gb300 import transform_bits, workspace_bytes
+    from oracle import stages as S
+    for na, nb in [(1, 1), (33, 32), (33, 33), (1 << 16, 1 << 16), (1 << 24, 1 << 24), (1 << 30, 1 << 30),
+                   (5, 1 << 20), (1 << 36, 1 << 36)]:
+        n = S.transform_length(na, nb)
+        assert transform_bits(na, nb) == n
+        assert workspace_bytes(na, nb) == 3 * ((n // 8 + 255) // 256 * 256)
+    assert transform_bits(0, 5) == 0 and workspace_bytes(7, 0) == 0
+    assert workspace_bytes(1 << 36, (1 << 36) + 2) == 0            # n = 2^38 > 2^37
+
+
+def test_status_strings(lib):
+    assert lib.gf2x_status_string(0) == b"GF2X_OK"
+    assert lib.gf2x_status_string(2) == b"GF2X_ETOOBIG"
+
+
+def test_null_context_rejected(lib):
+    assert lib.gf2x_mul(None, None, 1, None, 1, None, None, 0, None) == 1      # EINVAL
+    assert lib.gf2x_basis_cvt(None, None, 64, None) == 1
+    assert lib.gf2x_ctx_create(None, 0) == 1
+
+
+def test_no_device_path_reports_enodev(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.gf2x_ctx_create(ctypes.byref(h), 0) == 6                      # ENODEV, no fallback

@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle -- needs a GPU.
+
+Integer work, so the bar is bit-exact everywhere.  Stage by stage (Alg. 1,
+4, 2, Alg. 5 line 7) against ``oracle.stages``; end to end (Alg. 5) against
+the Karatsuba oracle where it finishes and against the modular checker at
+2^30-bit operands; the forward transform sampled against evaluation at the
+partition (Eq. 8) at full size.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import clmul as O
+from oracle import field as F
+from oracle import stages as S
+
+pytestmark = pytest.mark.gpu
+
+rng = random.Random(0xB300)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1803_11301_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(words):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(words, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def rand_words(n):
+    return synth.splitmix64(rng.getrandbits(63), n)
+
+
+# ------------------------------------------------------------------ stages
+def test_pointwise_field_product(ctx):
+    for count in [1, 31, 1000, 1 << 16]:
+        a, b = rand_words(count), rand_words(count)
+        a[:3] = [0, 1, 1 << 63]
+        b[:3] = [5, 1 << 63, 2]
+        got = host(ctx.pointwise(dev(a), dev(b)))
+        assert np.array_equal(got, F.gf_mul_arr(a, b))
+
+
+@pytest.mark.parametrize("L", [64, 128, 256, 1024, 4096, 1 << 14, 1 << 16])
+def test_basis_cvt_matches_alg1(ctx, L):
+    f = O.words_to_int(rand_words(L // 64))
+    t = dev(O.int_to_words(f, L))
+    ctx.basis_cvt(t, L)
+    assert O.words_to_int(host(t)) == S.basis_cvt(f, L)
+    ctx.ibasis_cvt(t, L)
+    assert O.words_to_int(host(t)) == f
+
+
+@pytest.mark.parametrize("L", [1 << 17, 1 << 20, 1 << 24])
+def test_basis_cvt_wide_steps_by_evaluation(ctx, L):
+    # beyond one tile: check sum_k g_k X_k(beta) = f(beta) at random beta, and the inverse
+    w = rand_words(L // 64)
+    t = dev(w)
+    ctx.basis_cvt(t, L)
+    g = host(t)
+    for _ in range(3):
+        beta = rng.getrandbits(64)
+        assert S.novelpoly_eval(g, L, beta) == O.eval_at(w, L, beta)
+    ctx.ibasis_cvt(t, L)
+    assert np.array_equal(host(t), w)
+
+
+@pytest.mark.parametrize("n", [64, 128, 512, 2048, 4096, 1 << 13, 1 << 15])
+def test_encode_decode_match_alg4(ctx, n):
+    A = O.words_to_int(rand_words(n // 64))
+    f = ctx.encode(dev(O.int_to_words(A, n)), n)
+    assert np.array_equal(host(f), S.encode(A, n))
+    back = ctx.decode(f, n)
+    assert O.words_to_int(host(back)) == A
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 5, 6, 9, 12, 14])
+def test_butterfly_matches_alg2(ctx, l):
+    n = 64 << l
+    tw = S.Twiddles(l)
+    g = rand_words(1 << l)
+    t = dev(g)
+    ctx.butterfly(t, n)
+    y = host(t)
+    assert np.array_equal(y, S.butterfly(g, tw))
+    ctx.ibutterfly(t, n)
+    assert np.array_equal(host(t), g)
+
+
+@pytest.mark.parametrize("nbits", [64, 1000, 1 << 13, 1 << 16])
+def test_forward_path_is_evaluation_at_sigma(ctx, nbits):
+    # BasisCvt -> Encode -> Butterfly gives A(alpha + u_k) (Eq. 8)
+    n = 2 * S.next_pow2(nbits) if nbits > 32 else 64
+    l = n.bit_length() - 1 - 6
+    w = synth.mask_tail(rand_words((nbits + 63) // 64), nbits)
+    buf = np.zeros(n // 64, dtype=np.uint64)
+    buf[: len(w)] = w
+    t = dev(buf)
+    ctx.basis_cvt(t, max(64, S.next_pow2(nbits)))
+    f = ctx.encode(t, n)
+    ctx.butterfly(f, n)
+    y = host(f)
+    for k in sorted({0, 1, (1 << l) - 1} | {rng.randrange(1 << l) for _ in range(5)}):
+        assert int(y[k]) == O.eval_at(w, nbits, S.sigma_point(l, k)), k
+
+
+# -------------------------------------------------------------- end to end
+def check_product(ctx, na, nb, seed, square=False):
+    a = synth.operand(seed, na)
+    b = a if square else synth.operand(seed + 1, nb)
+    da = dev(a)
+    db = da if square else dev(b)
+    got = host(ctx.mul(da, na, db, nb))
+    want = O.mul(a, na, b, nb)
+    assert np.array_equal(got, want), (na, nb, seed)
+
+
+EDGE = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 33), (32, 33), (33, 33), (63, 1), (64, 1), (65, 1), (64, 64),
+        (65, 64), (100, 3), (127, 129), (1000, 1000), (1, 5000), (4095, 4097), (4096, 4096), (12345, 678),
+        (1 << 15, 1 << 15), (1 << 16, 1), (70001, 3333), (1 << 17, 1 << 17), (99999, 200001)]
+
+
+@pytest.mark.parametrize("na,nb", EDGE)
+def test_product_edge_sizes(ctx, na, nb):
+    check_product(ctx, na, nb, synth.config_seed(7, na ^ nb))
+
+
+def test_product_squaring_alias(ctx):
+    for n in [1, 64, 777, 1 << 16]:
+        check_product(ctx, n, n, synth.config_seed(8, n), square=True)
+
+
+def test_product_empty_operands(ctx):
+    import torch
+    a = dev(synth.operand(1, 100))
+    out = ctx.mul(a, 100, a, 0)
+    assert out.numel() == 0
+    torch.cuda.synchronize()
+
+
+def test_config1_many_seeds(ctx):
+    # 2^16 x 2^16, seeded uniform random bits (the small workload)
+    n = 1 << 16
+    for i in range(200):
+        check_product(ctx, n, n, synth.config_seed(1, 2 * i))
+
+
+def test_config2_bit_exact(ctx):
+    n = 1 << 24
+    for i in range(2):
+        check_product(ctx, n, n, synth.config_seed(2, 2 * i))
+
+
+def test_config3_modular_and_sampled_forward(ctx):
+    # 2^30 x 2^30: c mod p = (a mod p)(b mod p) mod p for 64 seeded irreducible p
+    na = nb = 1 << 30
+    a = synth.operand(synth.config_seed(3, 0), na)
+    b = synth.operand(synth.config_seed(3, 1), nb)
+    c = host(ctx.mul(dev(a), na, dev(b), nb))
+    lows = O.random_irreducibles(synth.config_seed(3, 99), 64)
+    ok = O.modcheck(a, na, b, nb, c, na + nb - 1, lows)
+    assert ok.all(), int(ok.sum())
+    assert O.words_to_int(c[-1:]) >> ((na + nb - 1) % 64) == 0       # tail written as zero
+
+
+def test_length_sweep_modular(ctx):
+    lows = O.random_irreducibles(synth.config_seed(3, 98), 16)
+    for e in range(18, 30, 3):
+        na = nb = 1 << e
+        a = synth.operand(synth.config_seed(3, 10 + e), na)
+        b = synth.operand(synth.config_seed(3, 40 + e), nb)
+        c = host(ctx.mul(dev(a), na, dev(b), nb))
+        assert O.modcheck(a, na, b, nb, c, na + nb - 1, lows).all(), e
+
+
+def test_host_entry_point(ctx):
+    for na, nb in [(1, 1), (1000, 77), (1 << 18, 1 << 17)]:
+        a = synth.operand(5 + na, na)
+        b = synth.operand(6 + nb, nb)
+        assert np.array_equal(ctx.mul_host(a, na, b, nb), O.mul(a, na, b, nb))
+
+
+# --------------------------------------------------------------- errors
+def test_argument_errors(ctx):
+    from paper_1803_11301_gb300 import Gf2xError, load_library
+    import ctypes
+    lib = load_library()
+    a = dev(synth.operand(3, 256))
+    c = dev(np.zeros(8, np.uint64))
+    ws = ctx.workspace(1 << 16)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    big = (1 << 36) + 1
+    assert lib.gf2x_mul(ctx._h, P(a), big, P(a), big, P(c), P(ws), ws.numel(), None) == 2     # ETOOBIG
+    assert lib.gf2x_mul(ctx._h, P(a), 256, P(a), 200, P(c), P(ws), 16, None) == 7             # ENOSPACE
+    assert lib.gf2x_mul(ctx._h, P(a), 256, P(a), 200, P(a), P(ws), ws.numel(), None) == 1    # c overlaps a
+    assert lib.gf2x_basis_cvt(ctx._h, P(a), 96, None) == 1                                     # not a power of 2
+    with pytest.raises(Gf2xError):
+        ctx.encode(a, 100)
+    assert ctx.stream_status() == 0

@@ -166,3 +166,18 @@ def test_transform_length_rule():
     assert S.transform_length(33, 32) == 64
     assert S.transform_length(33, 33) == 128
     assert S.transform_length(1 << 30, 1 << 30) == 1 << 31
+
+
+@pytest.mark.parametrize("L", [64, 256, 512, 4096, 1 << 14])
+def test_novelpoly_eval_is_the_definition(L):
+    # sum_k g_k X_k(beta) = f(beta) when g = BasisCvt(f); and equals the slow expansion
+    for _ in range(3):
+        f = rng.getrandbits(L)
+        g = S.basis_cvt(f, L)
+        beta = rng.getrandbits(64)
+        assert S.novelpoly_eval(O.int_to_words(g, L), L, beta) == O.eval_at(O.int_to_words(f, L), L, beta)
+    if L <= 256:
+        g = rng.getrandbits(L)
+        beta = rng.getrandbits(64)
+        f = S.novelpoly_expand(g, L)
+        assert S.novelpoly_eval(O.int_to_words(g, L), L, beta) == O.eval_at(O.int_to_words(f, L), L, beta)
