@@ -368,6 +368,38 @@ def run_gpu(args, world, rank, local):
     ctx.close()
 
 
+def run_stage(args):
+    """One stage of Alg. 5 on its own, through its C-ABI entry point (for profiling)."""
+    import torch
+    from paper_1803_11301_gb300 import Context, build as lib_build
+    lib_build.build()
+    ctx = Context(0)
+    n = 64 << args.log2_points
+    x = torch.from_numpy(synth.splitmix64(7, n // 64).view(np.int64)).cuda()
+    y = torch.empty_like(x)
+    fns = {
+        "butterfly": lambda: ctx.butterfly(x, n),
+        "ibutterfly": lambda: ctx.ibutterfly(x, n),
+        "basis_cvt": lambda: ctx.basis_cvt(x, n),
+        "ibasis_cvt": lambda: ctx.ibasis_cvt(x, n),
+        "encode": lambda: ctx.encode(x, n, out=y),
+        "decode": lambda: ctx.decode(x, n, out=y),
+        "pointwise": lambda: ctx.pointwise(x, x, out=y),
+    }
+    fn = fns[args.stage]
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    for _ in range(args.steps):
+        fn()
+    prof = ctx.profile_read()
+    ms, launches = prof[args.stage]
+    print(json.dumps({"stage": args.stage, "points": n // 64, "transform_bits": n, "steps": args.steps,
+                      "ms_per_call": ms / args.steps, "launches_per_call": launches / args.steps}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,7 +409,14 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage", default=None,
+                    choices=["butterfly", "ibutterfly", "basis_cvt", "ibasis_cvt", "encode", "decode", "pointwise"],
+                    help="time one stage alone through its entry point (profiling aid)")
+    ap.add_argument("--log2-points", type=int, default=24, help="n_p = 2^this GF(2^64) points for --stage")
     args = ap.parse_args()
+    if args.stage:
+        run_stage(args)
+        return
     if args.warmup < 3 and args.impl == "gf2x":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
