@@ -101,6 +101,29 @@ GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64
                           const uint64_t *b_host, uint64_t nb_bits, uint64_t *c_host,
                           void *workspace, size_t ws_bytes, void *stream);
 
+/* The product for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment convenience.  Some callers cannot call
+ * cudaMalloc or any allocator: a framework that has reserved the whole device
+ * for its own memory pool, or a code path where entering an allocator is not
+ * allowed.  This call takes no workspace: it runs gf2x_mul on a fixed scratch
+ * array of 3 * GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8 bytes (768 KiB) that lives in
+ * the library's device memory; every GPU that loads the library holds that
+ * array until the process exits.  It allocates nothing.
+ *   Limit: transform length n <= GF2X_NOALLOC_MAX_TRANSFORM_BITS (2^21 bits,
+ *   e.g. two operands of 2^20 bits); larger products return GF2X_ETOOBIG and
+ *   enqueue nothing.  Other arguments and results as for gf2x_mul.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls, on every stream of a device, use the same array, which
+ *   keeps the last call's contents (a call never reads scratch it has not
+ *   written).  Calls whose work overlaps on the GPU race on the array: order
+ *   them on one stream, or synchronise between them. */
+#define GF2X_NOALLOC_MAX_TRANSFORM_BITS (1ull << 21)
+GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
+                                      const uint64_t *b, uint64_t nb_bits, uint64_t *c,
+                                      void *stream);
+
 /* Read, and reset to GF2X_OK, the context's device status word after the
  * work already enqueued on `stream` has finished (synchronises the stream).
  * Device code records bounded-wait expiry (GF2X_ETIMEOUT) there; it never

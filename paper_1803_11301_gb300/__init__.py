@@ -39,6 +39,7 @@ ABI_FUNCTIONS = {
     "gf2x_mul": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_host_workspace_bytes": (_SZ, [_U64, _U64]),
     "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
+    "gf2x_mul_noalloc": (_ST, [_P, _P, _U64, _P, _U64, _P, _P]),
     "gf2x_stream_status": (_ST, [_P, _P]),
     "gf2x_basis_cvt": (_ST, [_P, _P, _U64, _P]),
     "gf2x_ibasis_cvt": (_ST, [_P, _P, _U64, _P]),
