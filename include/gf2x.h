@@ -76,7 +76,8 @@ GF2X_API void gf2x_ctx_destroy(gf2x_ctx *ctx);
 GF2X_API uint64_t gf2x_transform_bits(uint64_t na_bits, uint64_t nb_bits);
 
 /* Device workspace in bytes that gf2x_mul needs for these operand lengths
- * (three buffers of n/8 bytes, 256-byte aligned). */
+ * (three buffers of n/8 bytes, 256-byte aligned, and 256 bytes reserved for
+ * device-side state). */
 GF2X_API size_t gf2x_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
 
 /* c = a * b in GF(2)[x]: FP_Polymul, Alg. 5 (Sec. 3.4), on `stream`.
@@ -87,7 +88,13 @@ GF2X_API size_t gf2x_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
  *   workspace  device, >= gf2x_workspace_bytes(na, nb) bytes, 256-aligned;
  *              contents on entry are ignored, on exit undefined.
  * All device pointers 8-byte aligned.  na == 0 or nb == 0 is valid and
- * writes nothing. */
+ * writes nothing.
+ * Repeated calls: from the second call with the same a, b, c, workspace and
+ * sizes on, the kernel sequence is replayed from a captured CUDA graph (at
+ * most 16 are kept per context, least recently used dropped); the contents of
+ * the buffers may change between calls.  Set GF2X_GRAPHS=0 in the environment
+ * before creating the context to launch kernels one by one instead.  A context
+ * is not thread-safe: serialise calls that share it. */
 GF2X_API gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
                      const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                      void *workspace, size_t ws_bytes, void *stream);
@@ -106,7 +113,7 @@ GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64
  * cudaMalloc or any allocator: a framework that has reserved the whole device
  * for its own memory pool, or a code path where entering an allocator is not
  * allowed.  This call takes no workspace: it runs gf2x_mul on a fixed scratch
- * array of 3 * GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8 bytes (768 KiB) that lives in
+ * array of 3 * GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8 + 256 bytes (768 KiB) that lives in
  * the library's device memory; every GPU that loads the library holds that
  * array until the process exits.  It allocates nothing.
  *   Limit: transform length n <= GF2X_NOALLOC_MAX_TRANSFORM_BITS (2^21 bits,
@@ -123,6 +130,13 @@ GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64
 GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
                                       const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                                       void *stream);
+
+/* Self-test of the bounded device-side waits: launches one block that waits
+ * on a grid barrier for an arrival that never comes.  The wait gives up after
+ * a short limit (milliseconds), records GF2X_ETIMEOUT in the context status
+ * word and returns, so the context stays usable; read it with
+ * gf2x_stream_status.  The paper has no counterpart (failure detection). */
+GF2X_API gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream);
 
 /* Read, and reset to GF2X_OK, the context's device status word after the
  * work already enqueued on `stream` has finished (synchronises the stream).

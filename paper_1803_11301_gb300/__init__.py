@@ -41,6 +41,7 @@ ABI_FUNCTIONS = {
     "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_mul_noalloc": (_ST, [_P, _P, _U64, _P, _U64, _P, _P]),
     "gf2x_stream_status": (_ST, [_P, _P]),
+    "gf2x_selftest_wait_timeout": (_ST, [_P, _P]),
     "gf2x_basis_cvt": (_ST, [_P, _P, _U64, _P]),
     "gf2x_ibasis_cvt": (_ST, [_P, _P, _U64, _P]),
     "gf2x_encode": (_ST, [_P, _P, _U64, _P, _P]),
@@ -210,6 +211,10 @@ class Context:
         la = (_U64 * n)()
         self._lib.gf2x_profile_read(self._h, ms, la, n)
         return {self._lib.gf2x_stage_name(k).decode(): (ms[k], int(la[k])) for k in range(n)}
+
+    def selftest_wait_timeout(self, stream=None):
+        """Launch a bounded wait that must run out; the status word then reads GF2X_ETIMEOUT."""
+        _check(self._lib.gf2x_selftest_wait_timeout(self._h, self._stream(stream)), "gf2x_selftest_wait_timeout")
 
     def stream_status(self, stream=None) -> int:
         return int(self._lib.gf2x_stream_status(self._h, self._stream(stream)))

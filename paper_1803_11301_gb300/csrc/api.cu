@@ -4,11 +4,12 @@
 //
 // FP_Polymul (Alg. 5) on one stream, three workspace buffers X, Y, T of n/64
 // words each:
-//   T <- a (masked, zero-padded to n bits); BasisCvt(T, L_a); X <- Encode(T);
-//   Butterfly(X)                                                 (lines 1-3)
-//   T <- b ...; Y <- Encode(T); Butterfly(Y)                     (lines 4-6)
-//   X <- X * Y pointwise                                         (line 7)
-//   iButterfly(X); T <- Decode(X); iBasisCvt(T, n); c <- T        (lines 8-10)
+//   T <- a (masked, zero-padded to n bits); BasisCvt(T, L_a); X <- Encode(T)
+//   T <- b ...;                                       Y <- Encode(T)   (lines 1-2, 4-5)
+//   top Butterfly layers of X and Y                                    (lines 3, 6)
+//   one kernel per 2^11-point tile: low layers of both Butterflies,
+//     X <- X * Y, low layers of the iButterfly                        (lines 3, 6, 7, 8)
+//   top iButterfly layers of X; T <- Decode(X); iBasisCvt(T, n); c <- T (lines 8-10)
 // BasisCvt runs on L_a = max(64, next_pow2(na)) bits: the novelpoly basis
 // is triangular (deg X_k = k), so the coefficients at k >= L_a are zero.
 #include <cstdlib>
@@ -174,39 +175,68 @@ size_t buffer_bytes(u64 n) { return round_up((size_t)(n / 8)); }
 
 // ------------------------------------------------------------- profiling
 // Optional per-stage timing: a pair of CUDA events around every stage,
-// recorded on the stream the stage's kernels are launched on.  Read back (and
-// summed per stage) by gf2x_profile_read.
+// recorded on the stream the stage's kernels are launched on, summed per
+// stage by gf2x_profile_read.  Inside a captured CUDA graph the pair becomes
+// two event-record nodes (external events owned by the graph entry), so the
+// times of a replay are read the same way.
+struct Rec {
+    int stage;
+    cudaEvent_t e0, e1;
+    bool pooled;                        // events return to the pool after reading
+};
+
 struct Profiler {
-    std::vector<cudaEvent_t> ev;
-    std::vector<int> stage_of;          // per event pair
-    size_t used = 0;                    // events recorded since the last read
+    std::vector<cudaEvent_t> pool;      // free events
+    std::vector<Rec> pending;           // recorded, not yet read
     double ms[STAGE_COUNT] = {};
+    std::vector<Rec> *capture = nullptr; // set while a graph is being captured
+    Rec open{};
+    bool is_open = false;
 };
 
 Profiler *profiler(gf2x_ctx *ctx) { return (Profiler *)ctx->prof; }
+
+cudaEvent_t take_event(Profiler *p)
+{
+    cudaEvent_t e = nullptr;
+    if (p->capture || p->pool.empty()) {
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+}
+
+void record(Profiler *p, cudaEvent_t e, cudaStream_t st)
+{
+    if (p->capture) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
 
 void stage_begin(gf2x_ctx *ctx, int stage, cudaStream_t st)
 {
     ctx->stage = stage;
     if (!ctx->profiling) return;
     Profiler *p = profiler(ctx);
-    while (p->ev.size() < p->used + 2) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return;
-        p->ev.push_back(e);
-    }
-    p->stage_of.resize(p->ev.size() / 2 + 1);
-    p->stage_of[p->used / 2] = stage;
-    cudaEventRecord(p->ev[p->used], st);
+    cudaEvent_t e = take_event(p);
+    if (!e) return;
+    p->open = Rec{stage, e, nullptr, p->capture == nullptr};
+    p->is_open = true;
+    record(p, e, st);
 }
 
 void stage_end(gf2x_ctx *ctx, cudaStream_t st)
 {
     if (!ctx->profiling) return;
     Profiler *p = profiler(ctx);
-    if (p->ev.size() < p->used + 2) return;
-    cudaEventRecord(p->ev[p->used + 1], st);
-    p->used += 2;
+    if (!p->is_open) return;
+    p->is_open = false;
+    cudaEvent_t e = take_event(p);
+    if (!e) return;
+    p->open.e1 = e;
+    record(p, e, st);
+    (p->capture ? p->capture : &p->pending)->push_back(p->open);
 }
 
 struct StageScope {
@@ -216,7 +246,46 @@ struct StageScope {
     ~StageScope() { stage_end(ctx, st); }
 };
 
-// The forward half of Alg. 5 for one operand: lines 1-3 (or 4-6).
+// ---------------------------------------------------------- graph cache
+// gf2x_mul replays a captured CUDA graph when it is called again with the same
+// operands, result, workspace and sizes: the second such call captures the
+// kernel sequence on a private stream and every later call launches the graph
+// into the caller's stream (one launch instead of ~15-40).
+struct GraphEntry {
+    const u64 *a, *b;
+    u64 na, nb;
+    u64 *c;
+    void *ws;
+    bool profiling;
+    cudaGraphExec_t exec;
+    unsigned long long launches[STAGE_COUNT];
+    std::vector<Rec> recs;
+    unsigned long long stamp;
+};
+
+struct GraphCache {
+    std::vector<GraphEntry> entries;
+    struct Key { const u64 *a, *b; u64 na, nb; u64 *c; void *ws; };
+    std::vector<Key> seen;              // keys called once, not captured yet
+    cudaStream_t cap = nullptr;
+    unsigned long long clock = 0;
+    bool disabled = false;
+};
+
+constexpr size_t kMaxGraphs = 16;
+
+GraphCache *graphs(gf2x_ctx *ctx) { return (GraphCache *)ctx->graphs; }
+
+void destroy_entry(GraphEntry &g)
+{
+    cudaGraphExecDestroy(g.exec);
+    for (Rec &r : g.recs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+}
+
+// Lines 1-2 (or 4-5) of Alg. 5 for one operand: BasisCvt and Encode into F.
 gf2x_status forward(gf2x_ctx *ctx, const u64 *src, u64 nsrc, u64 n, u64 *T, u64 *F, cudaStream_t st)
 {
     const int l = log2_u64(n) - 6;
@@ -225,7 +294,6 @@ gf2x_status forward(gf2x_ctx *ctx, const u64 *src, u64 nsrc, u64 n, u64 *T, u64 
     { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, src, nsrc, T, n / 64, st)); }
     { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, st)); }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, F, st)); }
-    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, F, l, false, st)); }
     return GF2X_OK;
 }
 
@@ -245,11 +313,96 @@ gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb
         s = forward(ctx, b, nb, n, T, Y, st);
         if (s != GF2X_OK) return s;
     }
-    { StageScope s(ctx, STAGE_POINTWISE, st); TRY(gf2x::pointwise(ctx, X, square ? X : Y, X, n / 64, st)); }
-    { StageScope s(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly(ctx, X, l, true, st)); }
+    // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
+    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, X, square ? nullptr : Y, l, st)); }
+    { StageScope s(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, square ? X : Y, l, st)); }
+    { StageScope s(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, st)); }
     { StageScope s(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, T, st)); }
     { StageScope s(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, st)); }
     { StageScope s(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, nc, c, st)); }
+    return GF2X_OK;
+}
+
+// gf2x_mul through the graph cache (falls back to direct launches while a key
+// is new, while the caller's stream is itself being captured, or when
+// GF2X_GRAPHS=0 is set in the environment).
+gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws, cudaStream_t st)
+{
+    GraphCache *gc = graphs(ctx);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (gc->disabled || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return mul_device(ctx, a, na, b, nb, c, ws, st);
+    for (GraphEntry &e : gc->entries) {
+        if (e.a == a && e.b == b && e.na == na && e.nb == nb && e.c == c && e.ws == ws &&
+            e.profiling == ctx->profiling) {
+            e.stamp = ++gc->clock;
+            if (cudaGraphLaunch(e.exec, st) != cudaSuccess) return GF2X_ECUDA;
+            for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
+            if (ctx->profiling)
+                for (const Rec &r : e.recs) profiler(ctx)->pending.push_back(r);
+            return GF2X_OK;
+        }
+    }
+    bool repeat = false;
+    for (size_t k = 0; k < gc->seen.size(); ++k) {
+        const GraphCache::Key &key = gc->seen[k];
+        if (key.a == a && key.b == b && key.na == na && key.nb == nb && key.c == c && key.ws == ws) {
+            repeat = true;
+            gc->seen.erase(gc->seen.begin() + (long)k);
+            break;
+        }
+    }
+    if (!repeat) {
+        if (gc->seen.size() >= 64) gc->seen.erase(gc->seen.begin());
+        gc->seen.push_back({a, b, na, nb, c, ws});
+        return mul_device(ctx, a, na, b, nb, c, ws, st);
+    }
+    // second call with this key: capture, instantiate, launch
+    if (!gc->cap && cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return mul_device(ctx, a, na, b, nb, c, ws, st);
+    GraphEntry e{};
+    e.a = a; e.b = b; e.na = na; e.nb = nb; e.c = c; e.ws = ws; e.profiling = ctx->profiling;
+    unsigned long long before[STAGE_COUNT];
+    for (int k = 0; k < STAGE_COUNT; ++k) before[k] = ctx->launches[k];
+    Profiler *p = profiler(ctx);
+    if (cudaStreamBeginCapture(gc->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return mul_device(ctx, a, na, b, nb, c, ws, st);
+    p->capture = &e.recs;
+    gf2x_status s = mul_device(ctx, a, na, b, nb, c, ws, gc->cap);
+    p->capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(gc->cap, &graph);
+    for (int k = 0; k < STAGE_COUNT; ++k) {       // captured, not run: count them per replay
+        e.launches[k] = ctx->launches[k] - before[k];
+        ctx->launches[k] = before[k];
+    }
+    if (s != GF2X_OK || ce != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        cudaGetLastError();
+        return s != GF2X_OK ? s : mul_device(ctx, a, na, b, nb, c, ws, st);
+    }
+    ce = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        cudaGetLastError();
+        return mul_device(ctx, a, na, b, nb, c, ws, st);
+    }
+    if (gc->entries.size() >= kMaxGraphs) {       // evict the least recently used
+        size_t old = 0;
+        for (size_t k = 1; k < gc->entries.size(); ++k)
+            if (gc->entries[k].stamp < gc->entries[old].stamp) old = k;
+        destroy_entry(gc->entries[old]);
+        gc->entries.erase(gc->entries.begin() + (long)old);
+    }
+    e.stamp = ++gc->clock;
+    gc->entries.push_back(e);
+    GraphEntry &ent = gc->entries.back();
+    if (cudaGraphLaunch(ent.exec, st) != cudaSuccess) return GF2X_ECUDA;
+    for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += ent.launches[k];
+    if (ctx->profiling)
+        for (const Rec &r : ent.recs) p->pending.push_back(r);
     return GF2X_OK;
 }
 
@@ -288,11 +441,18 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     if (!ctx) return GF2X_ENOMEM;
     ctx->device = device;
     ctx->prof = new (std::nothrow) Profiler();
-    if (!ctx->prof) { delete ctx; return GF2X_ENOMEM; }
+    ctx->graphs = new (std::nothrow) GraphCache();
+    if (!ctx->prof || !ctx->graphs) {
+        delete profiler(ctx);
+        delete graphs(ctx);
+        delete ctx;
+        return GF2X_ENOMEM;
+    }
+    if (const char *env = std::getenv("GF2X_GRAPHS")) graphs(ctx)->disabled = (env[0] == '0');
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
 
     u64 v[64];
-    auto fail = [&](gf2x_status st) { delete profiler(ctx); delete ctx; return st; };
+    auto fail = [&](gf2x_status st) { delete profiler(ctx); delete graphs(ctx); delete ctx; return st; };
     if (!cantor_basis(v)) return fail(GF2X_EINVAL);
     std::memcpy(ctx->cantor, v, sizeof v);
 
@@ -315,16 +475,17 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     std::memcpy(&host[6144], v, sizeof v);
 
     if (cudaMalloc(&ctx->d_tables, host.size() * sizeof(u64)) != cudaSuccess) return fail(GF2X_ENOMEM);
-    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_status, kAlign) != cudaSuccess) {
         cudaFree(ctx->d_tables);
         return fail(GF2X_ENOMEM);
     }
+    ctx->d_sync = (GridSync *)((char *)ctx->d_status + 128);
     ctx->d_cvt = ctx->d_tables;
     ctx->d_enc = ctx->d_tables + 2048;
     ctx->d_dec = ctx->d_tables + 4096;
     ctx->d_cantor = ctx->d_tables + 6144;
     if (cudaMemcpy(ctx->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(ctx->d_status, 0, kAlign) != cudaSuccess) {
         cudaFree(ctx->d_tables);
         cudaFree(ctx->d_status);
         return fail(GF2X_ECUDA);
@@ -337,8 +498,15 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx)
 {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    if (GraphCache *gc = graphs(ctx)) {
+        for (GraphEntry &e : gc->entries) destroy_entry(e);
+        if (gc->cap) cudaStreamDestroy(gc->cap);
+        delete gc;
+    }
     if (Profiler *p = profiler(ctx)) {
-        for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
+        for (Rec &r : p->pending)
+            if (r.pooled) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         delete p;
     }
     cudaFree(ctx->d_tables);
@@ -352,7 +520,7 @@ size_t gf2x_workspace_bytes(uint64_t na, uint64_t nb)
 {
     u64 n = transform_bits(na, nb);
     if (!n || n > kMaxTransformBits) return 0;
-    return 3 * buffer_bytes(n);
+    return 3 * buffer_bytes(n) + kAlign;          // + 256 bytes reserved for device-side state
 }
 
 gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *c,
@@ -373,7 +541,7 @@ gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64
         return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GF2X_ECUDA;
-    return mul_device(ctx, a, na, b, nb, c, ws, (cudaStream_t)stream);
+    return mul_graph(ctx, a, na, b, nb, c, ws, (cudaStream_t)stream);
 }
 
 size_t gf2x_host_workspace_bytes(uint64_t na, uint64_t nb)
@@ -406,7 +574,7 @@ gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, co
     u64 *dc = (u64 *)((char *)db + round_up(bb));
     TRY(cudaMemcpyAsync(da, a_host, ab, cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, st));
-    gf2x_status s = mul_device(ctx, da, na, db, nb, dc, ws, st);
+    gf2x_status s = mul_graph(ctx, da, na, db, nb, dc, ws, st);
     if (s != GF2X_OK) return s;
     TRY(cudaMemcpyAsync(c_host, dc, cb, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
@@ -499,10 +667,17 @@ gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, 
     return from_cuda(gf2x::pointwise(ctx, a, b, c, count, (cudaStream_t)stream));
 }
 
+gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    return from_cuda(gf2x::wait_timeout_probe(ctx, ctx->d_sync, (cudaStream_t)stream));
+}
+
 const char *gf2x_stage_name(int stage)
 {
     static const char *names[STAGE_COUNT] = {"load", "basis_cvt", "encode", "butterfly", "pointwise",
-                                             "ibutterfly", "decode", "ibasis_cvt", "store"};
+                                             "ibutterfly", "decode", "ibasis_cvt", "store", "bottom_fused"};
     return (stage >= 0 && stage < STAGE_COUNT) ? names[stage] : "unknown";
 }
 
@@ -513,8 +688,10 @@ gf2x_status gf2x_profile_enable(gf2x_ctx *ctx, int enable)
     if (!ctx) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     Profiler *p = profiler(ctx);
-    if (p->used) cudaEventSynchronize(p->ev[p->used - 1]);
-    p->used = 0;
+    if (!p->pending.empty()) cudaEventSynchronize(p->pending.back().e1);
+    for (Rec &r : p->pending)
+        if (r.pooled) { p->pool.push_back(r.e0); p->pool.push_back(r.e1); }
+    p->pending.clear();
     for (double &m : p->ms) m = 0;
     for (auto &l : ctx->launches) l = 0;
     ctx->profiling = enable != 0;
@@ -526,13 +703,14 @@ int gf2x_profile_read(gf2x_ctx *ctx, double *ms, uint64_t *launches, int max_sta
     if (!ctx) return -1;
     DeviceGuard g(ctx->device);
     Profiler *p = profiler(ctx);
-    if (p->used) {
-        cudaEventSynchronize(p->ev[p->used - 1]);
-        for (size_t k = 0; k + 1 < p->used; k += 2) {
+    if (!p->pending.empty()) {
+        cudaEventSynchronize(p->pending.back().e1);
+        for (Rec &r : p->pending) {
             float t = 0;
-            if (cudaEventElapsedTime(&t, p->ev[k], p->ev[k + 1]) == cudaSuccess) p->ms[p->stage_of[k / 2]] += t;
+            if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) p->ms[r.stage] += t;
+            if (r.pooled) { p->pool.push_back(r.e0); p->pool.push_back(r.e1); }
         }
-        p->used = 0;
+        p->pending.clear();
     }
     int n = max_stages < STAGE_COUNT ? max_stages : STAGE_COUNT;
     for (int k = 0; k < n; ++k) {

@@ -1,0 +1,335 @@
+// Butterfly / iButterfly (Alg. 2, Sec. 2.3.2) with several layers per pass.
+//
+// Layer i works on blocks of 2^(i+1) points starting at s = blk 2^(i+1) and
+// multiplies by c = s_i(alpha + u_s).  By Eq. 4 (s_i shifts Cantor
+// coordinates right by i) and alpha = v_{l+32}:
+//     c = v_{l+32-i} + (element with Cantor coordinates 2 blk).
+//
+// Top passes (layers >= kBottom): a pass covers m <= 4 consecutive layers
+// [p, p+m).  The points it touches are split into columns: for fixed high
+// bits (>= p+m) and fixed low bits (< p), the 2^m points that differ in bits
+// [p, p+m) form one column, held by one thread in registers through all m
+// layers.  All columns of one group (same high bits) share the 2^m - 1
+// twiddles of the pass, so the block builds one multiplication table per
+// twiddle and reuses it for every column of the group.
+//
+// Bottom tile (layers < kBottom): 2^kBottom consecutive points in shared
+// memory, one layer after the other.  Layers whose twiddle is shared by at
+// least 2^kTableMin butterflies use tables; lower layers multiply with the
+// integer form.  In the fused mode the tile holds the matching tiles of both
+// transforms: forward A, forward B, pointwise product, inverse (Alg. 5 lines
+// 3, 6, 7, 8 for the low layers) in one pass over HBM.
+//
+// Multiplication table (method of four Russians, Sec. 4.5): for a fixed c,
+// tab[w][e] = c * (e x^(4w)) for the 16 four-bit windows w and e < 16, so
+// c*x = XOR_w tab[w][nibble_w(x)].  A window table is 16 x 8 bytes, exactly
+// the 32 shared-memory banks, so the 32 lanes of a warp never conflict.
+#include "gf2x_common.cuh"
+
+namespace gf2x {
+namespace {
+
+constexpr int kBottom = 11;          // bottom tile: 2^11 points (16 KiB per transform)
+constexpr int kTableMin = 7;         // layers >= 7 multiply through tables
+constexpr int kTopLayers = 4;        // layers per top pass
+constexpr int kThreads = 256;
+constexpr int kTab = 256;            // u64 entries per multiplication table
+
+// c * x^(4w) mod the field polynomial.
+__device__ __forceinline__ u64 mul_xpow(u64 c, int e)
+{
+    if (e == 0) return c;
+    return gf64_reduce(c >> (64 - e), c << e);
+}
+
+// Entry k (k = 16 w + e) of the table of c.
+__device__ __forceinline__ u64 table_entry(u64 c, int k)
+{
+    const int w = k >> 4, e = k & 15;
+    const u64 base = mul_xpow(c, 4 * w);
+    u64 lo = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if ((e >> b) & 1) {
+            lo ^= base << b;
+            if (b) hi ^= base >> (64 - b);
+        }
+    return gf64_reduce(hi, lo);
+}
+
+__device__ __forceinline__ u64 mul_tab(const u64 *__restrict__ tab, u64 x)
+{
+    u64 r = 0;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) r ^= tab[w * 16 + ((x >> (4 * w)) & 15)];
+    return r;
+}
+
+// Element with Cantor coordinates u (window tables of the context).
+__device__ __forceinline__ u64 cantor(const u64 *__restrict__ cvt, u64 u)
+{
+    u64 r = 0;
+    for (int k = 0; u; ++k, u >>= 8) r ^= cvt[k * 256 + (u & 255)];
+    return r;
+}
+
+// ------------------------------------------------------------------ top pass
+// Layers [p, p+M) of one or two transforms (blockIdx.y selects x0 or x1).
+// Grid.x covers (group, column chunk) pairs: `chunks` chunks of kThreads
+// columns per group, each block handling `per_block` consecutive chunks of
+// one group.  Tables: layer p + r has 2^(M-1-r) twiddles, stored from table
+// 2^(M-1-r) - 1 on; table j of that layer serves rows u with u >> (r+1) = j.
+template <int M, bool INV>
+__global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
+                                                       const u64 *__restrict__ cvt, const u64 *__restrict__ vb)
+{
+    extern __shared__ u64 tabs[];
+    u64 *x = blockIdx.y ? x1 : x0;
+    const u64 first = (u64)blockIdx.x * per_block;
+    const u64 group = first / chunks;
+    constexpr int ntab = (1 << M) - 1;
+    for (int k = threadIdx.x; k < ntab * kTab; k += kThreads) {
+        const int t = k / kTab, e = k % kTab;
+        const int lvl = 31 - __clz(t + 1);              // layer r = M-1-lvl holds 2^lvl tables
+        const int r = M - 1 - lvl;
+        const int j = t - ((1 << lvl) - 1);
+        const u64 blk = (group << lvl) | (u64)j;        // block index at layer p + r
+        const u64 c = vb[l + 32 - (p + r)] ^ cantor(cvt, blk << 1);
+        tabs[k] = table_entry(c, e);
+    }
+    __syncthreads();
+    const u64 stride = 1ull << p;
+    for (int ch = 0; ch < per_block; ++ch) {
+        const u64 chunk = first + ch;
+        if (chunk / chunks != group) break;
+        const u64 col = (chunk % chunks) * kThreads + threadIdx.x;
+        const u64 base = (group << (p + M)) + col;
+        u64 v[1 << M];
+#pragma unroll
+        for (int u = 0; u < (1 << M); ++u) v[u] = x[base + (u64)u * stride];
+#pragma unroll
+        for (int s2 = 0; s2 < M; ++s2) {
+            const int r = INV ? s2 : M - 1 - s2;
+            const int half = 1 << r;
+            const u64 *tl = tabs + (size_t)((1 << (M - 1 - r)) - 1) * kTab;
+#pragma unroll
+            for (int u = 0; u < (1 << M); ++u) {
+                if (u & half) continue;
+                const u64 *tb = tl + (size_t)(u >> (r + 1)) * kTab;
+                if (!INV) {
+                    v[u] ^= mul_tab(tb, v[u | half]);
+                    v[u | half] ^= v[u];
+                } else {
+                    v[u | half] ^= v[u];
+                    v[u] ^= mul_tab(tb, v[u | half]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < (1 << M); ++u) x[base + (u64)u * stride] = v[u];
+    }
+}
+
+// -------------------------------------------------------------- bottom tile
+enum BottomMode { BOTTOM_FWD = 0, BOTTOM_INV = 1, BOTTOM_FUSED = 2 };
+
+// One layer i (< bt) on a tile held in shared memory.  ctop = v_{l+32-i} +
+// Cantor((tile base) >> i); the block of local start s_lo adds Cantor(s_lo >> i).
+__device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, const u64 *__restrict__ cvt,
+                                           const u64 *tabs_i, bool inverse)
+{
+    const int nb = 1 << (bt - 1);                       // butterflies per layer
+    const int span = 1 << i;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        int blk = t >> i, j = t & (span - 1);
+        int s0 = (blk << (i + 1)) + j;
+        u64 x0 = a[s0], x1 = a[s0 + span];
+        if (tabs_i) {
+            const u64 *tb = tabs_i + (size_t)blk * kTab;
+            if (!inverse) {
+                x0 ^= mul_tab(tb, x1);
+                x1 ^= x0;
+            } else {
+                x1 ^= x0;
+                x0 ^= mul_tab(tb, x1);
+            }
+        } else {
+            u64 c = ctop ^ cvt[(blk << 1) & 255] ^ cvt[256 + ((blk << 1) >> 8)];   // Cantor(2 blk), 2 blk < 2^11
+            if (!inverse) {
+                x0 ^= gf64_mul(c, x1);
+                x1 ^= x0;
+            } else {
+                x1 ^= x0;
+                x0 ^= gf64_mul(c, x1);
+            }
+        }
+        a[s0] = x0;
+        a[s0 + span] = x1;
+    }
+}
+
+// Tables of layers [kTableMin, bt) for this tile: layer i has 2^(bt-1-i) twiddles.
+// Table offsets: layer i starts at tab_off(i) tables.
+__host__ __device__ __forceinline__ int tab_off(int bt, int i)
+{
+    // layers bt-1 (1 table), bt-2 (2), ..., i+1: sum = 2^(bt-1-i) - 1
+    return (1 << (bt - 1 - i)) - 1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
+                                                          const u64 *__restrict__ vb, int mode)
+{
+    extern __shared__ u64 sm[];
+    const int T = 1 << bt;
+    u64 *a = sm;
+    u64 *b = sm + T;
+    const bool fused = mode == BOTTOM_FUSED;
+    u64 *tabs = sm + (fused ? 2 : 1) * T;
+    const u64 base = (u64)blockIdx.x << bt;
+    const int tmin = bt > kTableMin ? kTableMin : bt;   // layers [tmin, bt) use tables
+    // load the tile(s)
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        a[k] = X[base + k];
+        if (fused) b[k] = Y[base + k];
+    }
+    // tables: layer i, local block j -> c = v_{l+32-i} + Cantor((base >> i) + 2 j)
+    const int ntab = tab_off(bt, tmin - 1) - 0;         // 2^(bt-tmin) - 1 tables in total
+    for (int k = threadIdx.x; k < ntab * kTab; k += blockDim.x) {
+        int t = k / kTab, e = k % kTab;
+        int i = bt - 1;
+        while (t >= tab_off(bt, i - 1)) --i;            // table t belongs to layer i
+        int j = t - tab_off(bt, i);
+        u64 c = vb[l + 32 - i] ^ cantor(cvt, (base >> i) + ((u64)j << 1));
+        tabs[k] = table_entry(c, e);
+    }
+    __syncthreads();
+    if (mode != BOTTOM_INV) {
+        for (int i = bt - 1; i >= 0; --i) {
+            u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+            const u64 *ti = i >= tmin ? tabs + (size_t)tab_off(bt, i) * kTab : nullptr;
+            tile_layer(a, bt, i, ctop, cvt, ti, false);
+            if (fused) tile_layer(b, bt, i, ctop, cvt, ti, false);
+            __syncthreads();
+        }
+    }
+    if (fused) {
+        for (int k = threadIdx.x; k < T; k += blockDim.x) a[k] = gf64_mul(a[k], b[k]);   // Alg. 5 line 7
+        __syncthreads();
+    }
+    if (mode != BOTTOM_FWD) {
+        for (int i = 0; i < bt; ++i) {
+            u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+            const u64 *ti = i >= tmin ? tabs + (size_t)tab_off(bt, i) * kTab : nullptr;
+            tile_layer(a, bt, i, ctop, cvt, ti, true);
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
+}
+
+size_t bottom_smem(int bt, bool fused)
+{
+    int tmin = bt > kTableMin ? kTableMin : bt;
+    size_t tables = (size_t)((1 << (bt - tmin)) - 1) * kTab;
+    return ((fused ? 2 : 1) * (size_t)(1 << bt) + tables) * sizeof(u64);
+}
+
+template <int M, bool INV>
+void launch_top(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
+                const u64 *cvt, const u64 *vb)
+{
+    size_t smem = (size_t)((1 << M) - 1) * kTab * sizeof(u64);
+    k_bfly_top<M, INV><<<grid, kThreads, smem, st>>>(x0, x1, l, p, chunks, per_block, cvt, vb);
+}
+
+cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, cudaStream_t st)
+{
+    // passes over layers [bt, l) in groups of <= kTopLayers; high to low for the forward transform
+    const int npass = (l - bt + kTopLayers - 1) / kTopLayers;
+    for (int k = 0; k < npass; ++k) {
+        const int idx = inverse ? k : npass - 1 - k;
+        const int p = bt + idx * kTopLayers;
+        const int m = (l - p) < kTopLayers ? (l - p) : kTopLayers;
+        const u64 chunks = (1ull << p) / kThreads;     // p >= kBottom, so 2^p >= 2048 columns
+        const u64 groups = (1ull << l) >> (p + m);
+        // chunks per block: up to 8 (tables built once per block), but keep at
+        // least two blocks per SM; a power of two, so it divides `chunks`
+        const u64 arrays = x1 ? 2 : 1;
+        u64 pb = chunks * groups * arrays / (2 * (u64)ctx->num_sms);
+        int per_block = 1;
+        while (per_block < 8 && (u64)(2 * per_block) <= pb && (u64)(2 * per_block) <= chunks) per_block *= 2;
+        dim3 grid((unsigned)(chunks * groups / per_block), (unsigned)arrays);
+        const u64 *cvt = ctx->d_cvt, *vb = ctx->d_cantor;
+        switch (m * 2 + (inverse ? 1 : 0)) {
+        case 2: launch_top<1, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 3: launch_top<1, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 4: launch_top<2, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 5: launch_top<2, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 6: launch_top<3, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 7: launch_top<3, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 8: launch_top<4, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        default: launch_top<4, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        }
+        count_launch(ctx);
+    }
+    return cudaGetLastError();
+}
+
+bool configured = false;
+
+void configure()
+{
+    if (configured) return;
+    cudaFuncSetAttribute(k_bfly_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true));
+    configured = true;
+}
+
+}  // namespace
+
+// Forward (or inverse) Butterfly of one transform of 2^l points.
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st)
+{
+    configure();
+    const int bt = l < kBottom ? l : kBottom;
+    if (!inverse) {
+        cudaError_t e = top_passes(ctx, x, nullptr, l, bt, false, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (bt > 0) {
+        k_bfly_bottom<<<(unsigned)(1ull << (l - bt)), kThreads, bottom_smem(bt, false), st>>>(
+            x, nullptr, l, bt, ctx->d_cvt, ctx->d_cantor, inverse ? BOTTOM_INV : BOTTOM_FWD);
+        count_launch(ctx);
+    }
+    if (inverse) return top_passes(ctx, x, nullptr, l, bt, true, st);
+    return cudaGetLastError();
+}
+
+// The top layers of both forward transforms in one launch per pass.
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, cudaStream_t st)
+{
+    configure();
+    const int bt = l < kBottom ? l : kBottom;
+    return top_passes(ctx, x0, x1, l, bt, false, st);
+}
+
+// Bottom layers of both forward transforms, the pointwise product and the
+// bottom layers of the inverse: X <- low layers of iButterfly(fwd(X) * fwd(Y)).
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, cudaStream_t st)
+{
+    configure();
+    const int bt = l < kBottom ? l : kBottom;
+    k_bfly_bottom<<<(unsigned)(1ull << (l - bt)), kThreads, bottom_smem(bt, true), st>>>(X, Y, l, bt, ctx->d_cvt,
+                                                                                         ctx->d_cantor, BOTTOM_FUSED);
+    count_launch(ctx);
+    return cudaGetLastError();
+}
+
+// The top layers of the inverse.
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, cudaStream_t st)
+{
+    configure();
+    const int bt = l < kBottom ? l : kBottom;
+    return top_passes(ctx, x, nullptr, l, bt, true, st);
+}
+
+}  // namespace gf2x

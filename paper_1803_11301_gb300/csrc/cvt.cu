@@ -12,12 +12,22 @@
 // with d = 2^k.  The outer and inner conversions are the same steps with h and
 // d scaled by the unit (tau bits, resp. 1 bit).  So BasisCvt is a fixed list
 // of (h, d) steps, each applied to every aligned 2h-bit segment; iBasisCvt is
-// the list reversed with each step inverted (lo update first, then the hi fix,
-// which is its own inverse).
+// the list reversed with each step inverted (lo update with the current hi,
+// then the hi fix, which is its own inverse).
 //
-// GPU mapping.  Steps with 2h <= one tile (2^16 bits) run back to back in
-// shared memory, one HBM read and write per run of such steps.  Wider steps
-// (segments larger than a tile) run as global passes over the array.
+// GPU mapping: one kernel per phase (kernel boundaries order the phases; in a
+// CUDA graph a boundary costs about 0.5 us, less than a software grid barrier,
+// measured at 1.7-2.7 us on GB300):
+//  * a run of consecutive steps with 2h <= one tile (2^18 bits) is one kernel:
+//    each block loads a tile into shared memory, applies the whole run, and
+//    writes it back (one HBM/L2 read and write per run);
+//  * a wider step is one kernel, in place: each lo word is owned by one
+//    thread, which also writes the quotient fix of the one hi word whose only
+//    reader it is (for d < 64 bits a thread owns four lo words, so hi[0],
+//    read by the owners of lo[0] and lo[1], has a single owner).
+//
+// The bounded grid barrier below is used by the wait self-test: a wait that
+// runs out records GF2X_ETIMEOUT in the context status word and returns.
 #include <vector>
 
 #include "gf2x_common.cuh"
@@ -25,17 +35,22 @@
 namespace gf2x {
 namespace {
 
-constexpr int kTileWordsLog = 10;               // 1024 words = 2^16 bits = 8 KiB
-constexpr int kMaxRun = 48;
+constexpr int kTileWordsLog = 12;               // 4096 words = 2^18 bits = 32 KiB
+constexpr int kMaxSteps = 96;                   // K <= 37 gives at most 90 steps
+constexpr int kThreads = 512;
 
 struct Step {
     u64 h, d;   // bits
 };
 
-struct StepRun {
-    int count;
-    u32 h[kMaxRun];
-    u32 d[kMaxRun];
+struct CvtPlan {
+    int nphase;
+    int inverse;
+    int tw_log;                     // tile = 2^tw_log words
+    u64 words;                      // L / 64
+    unsigned char wide[kMaxSteps];  // phase p: wide step (1) or tile run (0)
+    unsigned char first[kMaxSteps], count[kMaxSteps];
+    u64 h[kMaxSteps], d[kMaxSteps];
 };
 
 void build_steps(int K, u64 unit, std::vector<Step> &out)
@@ -49,10 +64,48 @@ void build_steps(int K, u64 unit, std::vector<Step> &out)
     build_steps(i, unit, out);                   // inner: inside every block
 }
 
+// ------------------------------------------------------------- grid barrier
+// Arrive-and-wait on the barrier in `gs` for `nblocks` blocks.  Returns false
+// (on every thread of the block) when the wait ran out or another block gave
+// up; the block must then return.
+__device__ bool grid_sync(GridSync *gs, unsigned nblocks, int *status, unsigned long long limit)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &gs->gen;
+        volatile unsigned *vabort = &gs->abort;
+        const unsigned my = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == my) {
+                if (*vabort) { ok = 0; break; }
+                if (++spins > limit) {
+                    atomicExch(&gs->abort, 1u);
+                    atomicCAS(status, (int)GF2X_OK, (int)GF2X_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 __device__ __forceinline__ u64 seg_mask(u32 h, u32 lo_bit, u32 hi_bit)
 {
-    // bits [lo_bit, hi_bit) of every 2h-bit segment of a 64-bit word
-    u64 one = (hi_bit - lo_bit >= 64) ? ~0ull : (((1ull << (hi_bit - lo_bit)) - 1) << lo_bit);
+    // bits [lo_bit, hi_bit) of every 2h-bit segment of a 64-bit word (h < 64)
+    u64 one = ((1ull << (hi_bit - lo_bit)) - 1) << lo_bit;
     u64 m = 0;
     for (u32 s = 0; s < 64; s += 2 * h) m |= one << s;
     return m;
@@ -85,19 +138,16 @@ __device__ __forceinline__ u64 lo_term(const u64 *seg, u64 hw, u64 d, u64 q, boo
     return v;
 }
 
-__global__ void k_cvt_tile(u64 *bits, int tw_log, StepRun run, int inverse)
+// A run of steps (all with 2h <= tile) on a tile in shared memory.
+__device__ void tile_run(u64 *sm, u64 tw, const CvtPlan &P, int first, int count)
 {
-    extern __shared__ u64 sm[];
-    const u64 tw = 1ull << tw_log;
-    u64 *g = bits + (u64)blockIdx.x * tw;
-    for (u64 w = threadIdx.x; w < tw; w += blockDim.x) sm[w] = g[w];
-    __syncthreads();
-    for (int s = 0; s < run.count; ++s) {
-        const u32 h = run.h[s], d = run.d[s];
+    const bool inverse = P.inverse != 0;
+    for (int s = first; s < first + count; ++s) {
+        const u64 h = P.h[s], d = P.d[s];
         if (h < 64) {                            // segments inside one word
-            const u64 ma = seg_mask(h, h, h + d);        // hi bottom d bits
-            const u64 mb = seg_mask(h, d, h);            // lo bits [d, h)
-            const u32 sh = h - d;
+            const u64 ma = seg_mask((u32)h, (u32)h, (u32)(h + d));   // hi bottom d bits
+            const u64 mb = seg_mask((u32)h, (u32)d, (u32)h);         // lo bits [d, h)
+            const u32 sh = (u32)(h - d);
             for (u64 w = threadIdx.x; w < tw; w += blockDim.x) {
                 u64 x = sm[w];
                 if (!inverse) {
@@ -131,34 +181,78 @@ __global__ void k_cvt_tile(u64 *bits, int tw_log, StepRun run, int inverse)
             __syncthreads();
         }
     }
+}
+
+// One wide step in place (segments larger than a tile, so h >= 2^18 bits, hw >= 4096 words).
+// Each thread owns four consecutive lo words.
+__global__ void __launch_bounds__(256) k_cvt_wide(u64 *bits, u64 words, u64 h, u64 d, int inverse)
+{
+    const u64 hw = h >> 6;
+    const int hl = __ffsll((long long)hw) - 1;
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * t >= words / 2) return;
+    const u64 w = 4 * t;                          // index among all lo words
+    const u64 seg = w >> hl, q0 = w & (hw - 1);
+    u64 *sp = bits + seg * 2 * hw;
+    u64 lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lo[k] = sp[q0 + k];
+    if (d >= 64) {
+        // lo[q] ^= hi'[q - dw]; the owner of lo[q] is the only reader of
+        // hi[q - dw] and writes its fix hi[r] ^= hi[2hw - dw + r] (r < dw)
+        const u64 dw = d >> 6;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const u64 q = q0 + k;
+            if (q < dw) continue;
+            const u64 r = q - dw;
+            const u64 hv = sp[hw + r];
+            u64 term = hv;
+            if (r < dw) {
+                const u64 top = sp[2 * hw - dw + r];
+                if (!inverse) term ^= top;       // the forward step uses the fixed hi
+                sp[hw + r] = hv ^ top;           // the fix is its own inverse
+            }
+            lo[k] ^= term;
+        }
+    } else {
+        // lo[q] ^= (hi'[q] << d) | (hi'[q-1] >> (64-d)); only hi[0] is fixed
+        u64 hv[5];
+        hv[0] = q0 > 0 ? sp[hw + q0 - 1] : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hv[k + 1] = sp[hw + q0 + k];
+        if (q0 == 0) {
+            const u64 top = sp[2 * hw - 1] >> (64 - d);
+            sp[hw] = hv[1] ^ top;
+            if (!inverse) hv[1] ^= top;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lo[k] ^= (hv[k + 1] << d) | (hv[k] >> (64 - d));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sp[q0 + k] = lo[k];
+}
+
+// A run of tile steps: one block per tile of 2^tw_log words.
+__global__ void __launch_bounds__(kThreads) k_cvt_tile(u64 *bits, CvtPlan P, int phase)
+{
+    extern __shared__ u64 sm[];
+    const u64 tw = 1ull << P.tw_log;
+    u64 *g = bits + (u64)blockIdx.x * tw;
+    for (u64 w = threadIdx.x; w < tw; w += blockDim.x) sm[w] = g[w];
+    __syncthreads();
+    tile_run(sm, tw, P, P.first[phase], P.count[phase]);
     for (u64 w = threadIdx.x; w < tw; w += blockDim.x) g[w] = sm[w];
 }
 
-// One wide step, lo half: every lo word of every segment.
-__global__ void k_cvt_lo(u64 *bits, u64 total_lo, u64 hw, u64 d, int inverse)
+// Bounded-wait self-test: one block waits for a second arrival that never
+// comes, so the wait runs out and records GF2X_ETIMEOUT.
+__global__ void k_wait_timeout_probe(GridSync *gs, int *status, unsigned long long limit)
 {
-    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total_lo) return;
-    const int hl = __ffsll((long long)hw) - 1;
-    u64 seg = t >> hl, q = t & (hw - 1);
-    u64 *sp = bits + seg * 2 * hw;
-    sp[q] ^= lo_term(sp, hw, d, q, !inverse);
+    grid_sync(gs, gridDim.x + 1, status, limit);
 }
 
-// One wide step, the quotient fix of the hi half (runs after k_cvt_lo).
-__global__ void k_cvt_fix(u64 *bits, u64 nseg, u64 hw, u64 d)
-{
-    u64 nfix = d >= 64 ? (d >> 6) : 1;
-    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nseg * nfix) return;
-    const int fl = __ffsll((long long)nfix) - 1;
-    u64 seg = t >> fl, r = t & (nfix - 1);
-    u64 *sp = bits + seg * 2 * hw;
-    if (d >= 64) sp[hw + r] ^= sp[2 * hw - nfix + r];
-    else sp[hw] ^= sp[2 * hw - 1] >> (64 - d);
-}
-
-inline unsigned blocks_for(u64 n, unsigned threads) { return (unsigned)((n + threads - 1) / threads); }
+bool g_configured = false;
 
 }  // namespace
 
@@ -168,41 +262,55 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_
     while ((1ull << K) < L) ++K;
     std::vector<Step> steps;
     build_steps(K, 1, steps);
+    if (steps.empty()) return cudaSuccess;
     if (inverse) std::vector<Step>(steps.rbegin(), steps.rend()).swap(steps);
-
-    const u64 words = L >> 6;
-    int tw_log = 0;
-    while ((1ull << tw_log) < words && tw_log < kTileWordsLog) ++tw_log;
-    const u64 tile_bits = 64ull << tw_log;
-    const unsigned tile_threads = 256;
-
-    StepRun run;
-    run.count = 0;
-    auto flush = [&]() {
-        if (!run.count) return;
-        unsigned nblk = (unsigned)(words >> tw_log);
-        k_cvt_tile<<<nblk, tile_threads, (size_t)(8ull << tw_log), st>>>(bits, tw_log, run, inverse ? 1 : 0);
-        count_launch(ctx);
-        run.count = 0;
-    };
-    for (const Step &s : steps) {
-        if (2 * s.h <= tile_bits) {
-            if (run.count == kMaxRun) flush();
-            run.h[run.count] = (u32)s.h;
-            run.d[run.count] = (u32)s.d;
-            ++run.count;
-            continue;
-        }
-        flush();
-        const u64 hw = s.h >> 6;
-        const u64 total_lo = words / 2;
-        const u64 nseg = words / (2 * hw);
-        const u64 nfix = s.d >= 64 ? (s.d >> 6) : 1;
-        k_cvt_lo<<<blocks_for(total_lo, 256), 256, 0, st>>>(bits, total_lo, hw, s.d, inverse ? 1 : 0);
-        k_cvt_fix<<<blocks_for(nseg * nfix, 256), 256, 0, st>>>(bits, nseg, hw, s.d);
-        count_launch(ctx, 2);
+    if (!g_configured) {
+        cudaFuncSetAttribute(k_cvt_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
+        g_configured = true;
     }
-    flush();
+
+    CvtPlan P;
+    P.inverse = inverse ? 1 : 0;
+    P.words = L >> 6;
+    int tw_log = 0;
+    while ((1ull << tw_log) < P.words && tw_log < kTileWordsLog) ++tw_log;
+    P.tw_log = tw_log;
+    const u64 tile_bits = 64ull << tw_log;
+    P.nphase = 0;
+    for (size_t k = 0; k < steps.size(); ++k) {
+        P.h[k] = steps[k].h;
+        P.d[k] = steps[k].d;
+        const bool wide = 2 * steps[k].h > tile_bits;
+        if (wide || P.nphase == 0 || P.wide[P.nphase - 1]) {
+            P.wide[P.nphase] = wide ? 1 : 0;
+            P.first[P.nphase] = (unsigned char)k;
+            P.count[P.nphase] = 1;
+            ++P.nphase;
+        } else {
+            ++P.count[P.nphase - 1];
+        }
+    }
+    const u64 ntiles = P.words >> tw_log;
+    const u64 wide_threads = P.words / 8;         // four lo words per thread
+    for (int ph = 0; ph < P.nphase; ++ph) {
+        if (P.wide[ph]) {
+            const int s0 = P.first[ph];
+            k_cvt_wide<<<(unsigned)((wide_threads + 255) / 256), 256, 0, st>>>(bits, P.words, P.h[s0], P.d[s0],
+                                                                                P.inverse);
+        } else {
+            k_cvt_tile<<<(unsigned)ntiles, kThreads, (size_t)8 << tw_log, st>>>(bits, P, ph);
+        }
+        count_launch(ctx);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GridSync), st);
+    if (e != cudaSuccess) return e;
+    k_wait_timeout_probe<<<1, 32, 0, st>>>(gs, ctx->d_status, 1ull << 14);
+    count_launch(ctx);
     return cudaGetLastError();
 }
 

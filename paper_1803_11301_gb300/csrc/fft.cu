@@ -1,5 +1,5 @@
-// Encode / Decode (Alg. 4), Butterfly / iButterfly (Alg. 2), the pointwise
-// product (Alg. 5 line 7) and the bit-array load/store around them.
+// Encode / Decode (Alg. 4), the pointwise product (Alg. 5 line 7) and the
+// bit-array load/store around them.
 #include "gf2x_common.cuh"
 
 namespace gf2x {
@@ -102,33 +102,6 @@ __global__ void k_decode_small(const u64 *__restrict__ h, int l, const u64 *__re
     }
 }
 
-// ---------------------------------------------------------------- Butterfly
-// One layer i of Alg. 2 unrolled: block start s (a multiple of 2^(i+1)),
-// multiplier c = s_i(alpha + u_s).  By Eq. 4 s_i acts on Cantor coordinates as
-// a right shift, so c has coordinates (2^(l+32) xor s) >> i, i.e.
-// c = v_{l+32-i} + (element with coordinates s >> i).
-__global__ void k_butterfly_layer(u64 *__restrict__ x, u64 half, int i, u64 c_top, const u64 *__restrict__ cvt,
-                                  int inverse)
-{
-    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= half) return;
-    const u64 span = 1ull << i;
-    u64 blk = t >> i, j = t & (span - 1);
-    u64 s = blk << (i + 1);
-    u64 c = c_top ^ lin64(cvt, blk << 1);        // coordinates s >> i = 2 blk
-    u64 *p0 = x + s + j, *p1 = p0 + span;
-    u64 a = *p0, b = *p1;
-    if (!inverse) {
-        a ^= gf64_mul(c, b);
-        b ^= a;
-    } else {
-        b ^= a;
-        a ^= gf64_mul(c, b);
-    }
-    *p0 = a;
-    *p1 = b;
-}
-
 __global__ void k_pointwise(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *c, u64 count)
 {
     u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,18 +150,6 @@ cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t 
         k_decode<<<(unsigned)(rw / cols), 256, 0, st>>>(h, rw, ctx->d_dec, novel);
     }
     count_launch(ctx);
-    return cudaGetLastError();
-}
-
-cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st)
-{
-    const u64 half = (1ull << l) >> 1;
-    for (int k = 0; k < l; ++k) {
-        int i = inverse ? k : l - 1 - k;
-        k_butterfly_layer<<<blocks_for(half, 256), 256, 0, st>>>(x, half, i, ctx->cantor[l + 32 - i], ctx->d_cvt,
-                                                                 inverse ? 1 : 0);
-    }
-    count_launch(ctx, l);
     return cudaGetLastError();
 }
 

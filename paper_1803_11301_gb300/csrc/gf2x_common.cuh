@@ -65,11 +65,22 @@ __device__ __forceinline__ u64 lin64(const u64 *__restrict__ t, u64 x)
     return r;
 }
 
+// State of one grid-wide barrier (see cvt.cu); must be zero before a launch.
+struct GridSync {
+    unsigned count;   // blocks arrived in the current generation
+    unsigned gen;     // generation, bumped by the last arrival
+    unsigned abort;   // set when a wait ran out: every block returns
+    unsigned pad;
+};
+
 // ------------------------------------------------------------------ context
 // Stages of Alg. 5 as the profiler and the launch counter see them.
+// STAGE_BOTTOM is the fused low-layer kernel of gf2x_mul: the bottom layers of
+// both forward Butterflies, the pointwise product and the bottom layers of the
+// iButterfly; STAGE_BUTTERFLY / STAGE_IBUTTERFLY then hold the top layers.
 enum Gf2xStage {
     STAGE_LOAD = 0, STAGE_BASISCVT, STAGE_ENCODE, STAGE_BUTTERFLY, STAGE_POINTWISE,
-    STAGE_IBUTTERFLY, STAGE_DECODE, STAGE_IBASISCVT, STAGE_STORE, STAGE_COUNT
+    STAGE_IBUTTERFLY, STAGE_DECODE, STAGE_IBASISCVT, STAGE_STORE, STAGE_BOTTOM, STAGE_COUNT
 };
 
 struct gf2x_ctx {
@@ -81,6 +92,7 @@ struct gf2x_ctx {
     u64 *d_dec;         // 8 x 256: f_i -> bits                    (matrix R^{-1})
     u64 *d_cantor;      // v_0 .. v_63
     int *d_status;      // device status word (gf2x_status)
+    GridSync *d_sync;   // barrier state for the stage entry points
     u64 cantor[64];     // host copy of the Cantor basis
 
     // launch accounting and optional per-stage event timing (host side)
@@ -88,6 +100,7 @@ struct gf2x_ctx {
     unsigned long long launches[STAGE_COUNT];
     bool profiling;
     void *prof;                         // event pool, see api.cu
+    void *graphs;                       // CUDA graph cache of gf2x_mul, see api.cu
 };
 
 // Count one kernel launch against the current stage.
@@ -98,9 +111,13 @@ inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] +
 namespace gf2x {
 
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_t st);
+cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, cudaStream_t st);
 cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t st);
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st);
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, cudaStream_t st);
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, cudaStream_t st);
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, cudaStream_t st);
 cudaError_t pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
 cudaError_t load_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, u64 dst_words, cudaStream_t st);
 cudaError_t store_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, cudaStream_t st);

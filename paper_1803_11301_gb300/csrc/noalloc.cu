@@ -18,8 +18,9 @@
 namespace {
 
 // Scratch for the largest product this entry point accepts: three buffers
-// of n/8 bytes (see gf2x_workspace_bytes) for n = GF2X_NOALLOC_MAX_TRANSFORM_BITS.
-constexpr size_t kScratchBytes = 3 * (GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8);
+// of n/8 bytes and 256 bytes of barrier state (see gf2x_workspace_bytes) for
+// n = GF2X_NOALLOC_MAX_TRANSFORM_BITS.
+constexpr size_t kScratchBytes = 3 * (GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8) + 256;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchBytes / 8];
 

@@ -90,7 +90,7 @@ def test_encode_decode_match_alg4(ctx, n):
     assert O.words_to_int(host(back)) == A
 
 
-@pytest.mark.parametrize("l", [0, 1, 2, 5, 6, 9, 12, 14])
+@pytest.mark.parametrize("l", [0, 1, 2, 5, 6, 7, 8, 9, 11, 12, 14, 15, 17, 19])
 def test_butterfly_matches_alg2(ctx, l):
     n = 64 << l
     tw = S.Twiddles(l)
@@ -139,6 +139,24 @@ EDGE = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 33), (32, 33), (33, 33), (63, 1), (
 @pytest.mark.parametrize("na,nb", EDGE)
 def test_product_edge_sizes(ctx, na, nb):
     check_product(ctx, na, nb, synth.config_seed(7, na ^ nb))
+
+
+def test_repeated_calls_replay_with_new_contents(ctx):
+    # the same buffers and sizes on every call: calls 2.. replay a captured graph
+    import torch
+    na, nb = 50000, 123457
+    da = dev(np.zeros((na + 63) // 64, np.uint64))
+    db = dev(np.zeros((nb + 63) // 64, np.uint64))
+    out = torch.empty((na + nb - 1 + 63) // 64, dtype=torch.int64, device="cuda")
+    from paper_1803_11301_gb300 import workspace_bytes
+    ws = torch.empty(workspace_bytes(na, nb), dtype=torch.uint8, device="cuda")
+    for k in range(5):
+        a = synth.operand(synth.config_seed(10, 2 * k), na)
+        b = synth.operand(synth.config_seed(10, 2 * k + 1), nb)
+        da.copy_(dev(a))
+        db.copy_(dev(b))
+        ctx.mul(da, na, db, nb, out=out, workspace=ws)
+        assert np.array_equal(host(out), O.mul(a, na, b, nb)), k
 
 
 def test_product_squaring_alias(ctx):
@@ -197,6 +215,15 @@ def test_host_entry_point(ctx):
 
 
 # --------------------------------------------------------------- errors
+def test_bounded_wait_reports_timeout(ctx):
+    # a device-side wait that can never complete gives up and reports GF2X_ETIMEOUT
+    ctx.selftest_wait_timeout()
+    assert ctx.stream_status() == 5
+    assert ctx.stream_status() == 0                  # reading resets the status word
+    check_product(ctx, 70001, 3333, synth.config_seed(7, 1234))   # the context stays usable
+
+
+
 def test_argument_errors(ctx):
     from paper_1803_11301_gb300 import Gf2xError, load_library
     import ctypes
