@@ -14,23 +14,25 @@
 // twiddle and reuses it for every column of the group.
 //
 // Bottom tile (layers < kBottom): 2^kBottom consecutive points in shared
-// memory, one layer after the other.  Layers whose twiddle is shared by at
-// least 2^kTableMin butterflies use tables; lower layers multiply with the
-// integer form.  In the fused mode the tile holds the matching tiles of both
+// memory, one layer after the other.  Layers i >= kTableMin (twiddle shared by
+// 2^i butterflies per array) use tables, built kChunkTabs at a time; layers
+// 0..kTableMin-1 multiply with the integer form.  In the fused mode the tile holds the matching tiles of both
 // transforms: forward A, forward B, pointwise product, inverse (Alg. 5 lines
 // 3, 6, 7, 8 for the low layers) in one pass over HBM.
 //
 // Multiplication table (method of four Russians, Sec. 4.5): for a fixed c,
 // tab[w][e] = c * (e x^(4w)) for the 16 four-bit windows w and e < 16, so
 // c*x = XOR_w tab[w][nibble_w(x)].  A window table is 16 x 8 bytes, exactly
-// the 32 shared-memory banks, so the 32 lanes of a warp never conflict.
+// the 32 shared-memory banks, so the 32 lanes of a warp never conflict.  A
+// table is built from the 64 powers c x^k: each entry XORs at most four.
 #include "gf2x_common.cuh"
 
 namespace gf2x {
 namespace {
 
 constexpr int kBottom = 11;          // bottom tile: 2^11 points (16 KiB per transform)
-constexpr int kTableMin = 7;         // layers >= 7 multiply through tables
+constexpr int kTableMin = 6;         // bottom layers >= 6 multiply through tables
+constexpr int kChunkTabs = 16;       // bottom tables built at a time (32 KiB)
 constexpr int kTopLayers = 4;        // layers per top pass
 constexpr int kThreads = 256;
 constexpr int kTab = 256;            // u64 entries per multiplication table
@@ -42,27 +44,43 @@ __device__ __forceinline__ u64 mul_xpow(u64 c, int e)
     return gf64_reduce(c >> (64 - e), c << e);
 }
 
-// Entry k (k = 16 w + e) of the table of c.
-__device__ __forceinline__ u64 table_entry(u64 c, int k)
-{
-    const int w = k >> 4, e = k & 15;
-    const u64 base = mul_xpow(c, 4 * w);
-    u64 lo = 0, hi = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        if ((e >> b) & 1) {
-            lo ^= base << b;
-            if (b) hi ^= base >> (64 - b);
-        }
-    return gf64_reduce(hi, lo);
-}
-
+// Window w keeps entry e at slot e ^ w, so that the 16 threads writing one
+// window each (build) and the 32 lanes reading one window (lookup) touch
+// distinct bank pairs.
 __device__ __forceinline__ u64 mul_tab(const u64 *__restrict__ tab, u64 x)
 {
     u64 r = 0;
 #pragma unroll
-    for (int w = 0; w < 16; ++w) r ^= tab[w * 16 + ((x >> (4 * w)) & 15)];
+    for (int w = 0; w < 16; ++w) r ^= tab[w * 16 + ((((unsigned)(x >> (4 * w))) & 15u) ^ (unsigned)w)];
     return r;
+}
+
+__device__ __forceinline__ u64 mul_x(u64 p) { return (p << 1) ^ ((p >> 63) * GF2X_MOD_LOW); }
+
+// Build nt tables: thread (t, w) computes the powers c x^(4w+b), b < 4, of
+// twiddle c = twid(t) and writes the 16 entries of window w (Gray-code XORs).
+// Ends with __syncthreads().
+template <class F>
+__device__ __forceinline__ void build_tables(u64 *tabs, int nt, F twid)
+{
+    for (int k = threadIdx.x; k < nt * 16; k += blockDim.x) {
+        const int t = k >> 4, w = k & 15;
+        const u64 c = twid(t);
+        u64 p[4];
+        p[0] = mul_xpow(c, 4 * w);
+        p[1] = mul_x(p[0]);
+        p[2] = mul_x(p[1]);
+        p[3] = mul_x(p[2]);
+        u64 *dst = tabs + (size_t)t * kTab + w * 16;
+        u64 e = 0;
+        dst[0 ^ w] = 0;
+#pragma unroll
+        for (int g = 1; g < 16; ++g) {            // Gray code: flip the lowest set bit of g
+            e ^= p[(g & 1) ? 0 : (g & 2) ? 1 : (g & 4) ? 2 : 3];
+            dst[(g ^ (g >> 1)) ^ w] = e;
+        }
+    }
+    __syncthreads();
 }
 
 // Element with Cantor coordinates u (window tables of the context).
@@ -84,20 +102,17 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
                                                        const u64 *__restrict__ cvt, const u64 *__restrict__ vb)
 {
     extern __shared__ u64 tabs[];
+    constexpr int ntab = (1 << M) - 1;
     u64 *x = blockIdx.y ? x1 : x0;
     const u64 first = (u64)blockIdx.x * per_block;
     const u64 group = first / chunks;
-    constexpr int ntab = (1 << M) - 1;
-    for (int k = threadIdx.x; k < ntab * kTab; k += kThreads) {
-        const int t = k / kTab, e = k % kTab;
+    build_tables(tabs, ntab, [&](int t) {
         const int lvl = 31 - __clz(t + 1);              // layer r = M-1-lvl holds 2^lvl tables
         const int r = M - 1 - lvl;
         const int j = t - ((1 << lvl) - 1);
         const u64 blk = (group << lvl) | (u64)j;        // block index at layer p + r
-        const u64 c = vb[l + 32 - (p + r)] ^ cantor(cvt, blk << 1);
-        tabs[k] = table_entry(c, e);
-    }
-    __syncthreads();
+        return vb[l + 32 - (p + r)] ^ cantor(cvt, blk << 1);
+    });
     const u64 stride = 1ull << p;
     for (int ch = 0; ch < per_block; ++ch) {
         const u64 chunk = first + ch;
@@ -135,8 +150,7 @@ enum BottomMode { BOTTOM_FWD = 0, BOTTOM_INV = 1, BOTTOM_FUSED = 2 };
 
 // One layer i (< bt) on a tile held in shared memory.  ctop = v_{l+32-i} +
 // Cantor((tile base) >> i); the block of local start s_lo adds Cantor(s_lo >> i).
-__device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, const u64 *__restrict__ cvt,
-                                           const u64 *tabs_i, bool inverse)
+__device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, const u64 *__restrict__ cvt, bool inverse)
 {
     const int nb = 1 << (bt - 1);                       // butterflies per layer
     const int span = 1 << i;
@@ -144,36 +158,55 @@ __device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, cons
         int blk = t >> i, j = t & (span - 1);
         int s0 = (blk << (i + 1)) + j;
         u64 x0 = a[s0], x1 = a[s0 + span];
-        if (tabs_i) {
-            const u64 *tb = tabs_i + (size_t)blk * kTab;
-            if (!inverse) {
-                x0 ^= mul_tab(tb, x1);
-                x1 ^= x0;
-            } else {
-                x1 ^= x0;
-                x0 ^= mul_tab(tb, x1);
-            }
+        u64 c = ctop ^ cvt[(blk << 1) & 255] ^ cvt[256 + ((blk << 1) >> 8)];   // Cantor(2 blk), 2 blk < 2^11
+        if (!inverse) {
+            x0 ^= gf64_mul(c, x1);
+            x1 ^= x0;
         } else {
-            u64 c = ctop ^ cvt[(blk << 1) & 255] ^ cvt[256 + ((blk << 1) >> 8)];   // Cantor(2 blk), 2 blk < 2^11
-            if (!inverse) {
-                x0 ^= gf64_mul(c, x1);
-                x1 ^= x0;
-            } else {
-                x1 ^= x0;
-                x0 ^= gf64_mul(c, x1);
-            }
+            x1 ^= x0;
+            x0 ^= gf64_mul(c, x1);
         }
         a[s0] = x0;
         a[s0 + span] = x1;
     }
 }
 
-// Tables of layers [kTableMin, bt) for this tile: layer i has 2^(bt-1-i) twiddles.
-// Table offsets: layer i starts at tab_off(i) tables.
-__host__ __device__ __forceinline__ int tab_off(int bt, int i)
+// Layer i >= kTableMin on the tile(s): the 2^(bt-1-i) twiddles of the layer
+// c_j = v_{l+32-i} + Cantor((base >> i) + 2j) get tables kChunkTabs at a time;
+// each chunk's butterflies run on every array of the pass (A and B together).
+__device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, const u64 *__restrict__ cvt,
+                            const u64 *__restrict__ vb, u64 *tabs, bool inverse)
 {
-    // layers bt-1 (1 table), bt-2 (2), ..., i+1: sum = 2^(bt-1-i) - 1
-    return (1 << (bt - 1 - i)) - 1;
+    const int ntot = 1 << (bt - 1 - i);
+    const int span = 1 << i;
+    const u64 vtop = vb[l + 32 - i];
+    for (int j0 = 0; j0 < ntot; j0 += kChunkTabs) {
+        const int nt = ntot - j0 < kChunkTabs ? ntot - j0 : kChunkTabs;
+        build_tables(tabs, nt, [&](int t) { return vtop ^ cantor(cvt, (base >> i) + ((u64)(j0 + t) << 1)); });
+        for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
+            const int blk = j0 + (t >> i), jj = t & (span - 1);
+            const int s0 = (blk << (i + 1)) + jj;
+            const u64 *tb = tabs + (size_t)(blk - j0) * kTab;
+            u64 x0 = a[s0], x1 = a[s0 + span];
+            if (!inverse) {
+                x0 ^= mul_tab(tb, x1);
+                x1 ^= x0;
+            } else {
+                x1 ^= x0;
+                x0 ^= mul_tab(tb, x1);
+            }
+            a[s0] = x0;
+            a[s0 + span] = x1;
+            if (b) {
+                u64 y0 = b[s0], y1 = b[s0 + span];
+                y0 ^= mul_tab(tb, y1);
+                y1 ^= y0;
+                b[s0] = y0;
+                b[s0 + span] = y1;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
@@ -181,35 +214,26 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
 {
     extern __shared__ u64 sm[];
     const int T = 1 << bt;
-    u64 *a = sm;
-    u64 *b = sm + T;
     const bool fused = mode == BOTTOM_FUSED;
+    u64 *a = sm;
+    u64 *b = fused ? sm + T : nullptr;
     u64 *tabs = sm + (fused ? 2 : 1) * T;
     const u64 base = (u64)blockIdx.x << bt;
-    const int tmin = bt > kTableMin ? kTableMin : bt;   // layers [tmin, bt) use tables
-    // load the tile(s)
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
         a[k] = X[base + k];
         if (fused) b[k] = Y[base + k];
     }
-    // tables: layer i, local block j -> c = v_{l+32-i} + Cantor((base >> i) + 2 j)
-    const int ntab = tab_off(bt, tmin - 1) - 0;         // 2^(bt-tmin) - 1 tables in total
-    for (int k = threadIdx.x; k < ntab * kTab; k += blockDim.x) {
-        int t = k / kTab, e = k % kTab;
-        int i = bt - 1;
-        while (t >= tab_off(bt, i - 1)) --i;            // table t belongs to layer i
-        int j = t - tab_off(bt, i);
-        u64 c = vb[l + 32 - i] ^ cantor(cvt, (base >> i) + ((u64)j << 1));
-        tabs[k] = table_entry(c, e);
-    }
     __syncthreads();
     if (mode != BOTTOM_INV) {
         for (int i = bt - 1; i >= 0; --i) {
-            u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
-            const u64 *ti = i >= tmin ? tabs + (size_t)tab_off(bt, i) * kTab : nullptr;
-            tile_layer(a, bt, i, ctop, cvt, ti, false);
-            if (fused) tile_layer(b, bt, i, ctop, cvt, ti, false);
-            __syncthreads();
+            if (i >= kTableMin) {
+                table_layer(a, b, bt, i, l, base, cvt, vb, tabs, false);
+            } else {
+                const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+                tile_layer(a, bt, i, ctop, cvt, false);
+                if (fused) tile_layer(b, bt, i, ctop, cvt, false);
+                __syncthreads();
+            }
         }
     }
     if (fused) {
@@ -218,10 +242,13 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
     }
     if (mode != BOTTOM_FWD) {
         for (int i = 0; i < bt; ++i) {
-            u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
-            const u64 *ti = i >= tmin ? tabs + (size_t)tab_off(bt, i) * kTab : nullptr;
-            tile_layer(a, bt, i, ctop, cvt, ti, true);
-            __syncthreads();
+            if (i >= kTableMin) {
+                table_layer(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
+            } else {
+                const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+                tile_layer(a, bt, i, ctop, cvt, true);
+                __syncthreads();
+            }
         }
     }
     for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
@@ -229,9 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
 
 size_t bottom_smem(int bt, bool fused)
 {
-    int tmin = bt > kTableMin ? kTableMin : bt;
-    size_t tables = (size_t)((1 << (bt - tmin)) - 1) * kTab;
-    return ((fused ? 2 : 1) * (size_t)(1 << bt) + tables) * sizeof(u64);
+    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)kChunkTabs * kTab) * sizeof(u64);
 }
 
 template <int M, bool INV>
