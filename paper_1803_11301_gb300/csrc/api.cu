@@ -293,7 +293,7 @@ gf2x_status forward(gf2x_ctx *ctx, const u64 *src, u64 nsrc, u64 n, u64 *T, u64 
     if (L < 64) L = 64;
     { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, src, nsrc, T, n / 64, st)); }
     { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, st)); }
-    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, F, st)); }
+    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, F, L, st)); }
     return GF2X_OK;
 }
 
@@ -623,7 +623,7 @@ gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64
     if (!valid_n(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
-    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, (cudaStream_t)stream));
+    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, n, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)

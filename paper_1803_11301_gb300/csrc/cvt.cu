@@ -43,13 +43,18 @@ struct Step {
     u64 h, d;   // bits
 };
 
+enum PhaseKind { PHASE_TILE = 0, PHASE_WIDE = 1, PHASE_COLUMN = 2 };
+
 struct CvtPlan {
     int nphase;
     int inverse;
     int tw_log;                     // tile = 2^tw_log words
     u64 words;                      // L / 64
-    unsigned char wide[kMaxSteps];  // phase p: wide step (1) or tile run (0)
+    unsigned char kind[kMaxSteps];  // PhaseKind of phase p
     unsigned char first[kMaxSteps], count[kMaxSteps];
+    unsigned char ulog[kMaxSteps];  // column phase: unit of 2^ulog bits
+    unsigned char wlog[kMaxSteps];  // column phase: 2^wlog words per unit per block
+    unsigned char slog[kMaxSteps];  // column phase: 2^slog units per block
     u64 h[kMaxSteps], d[kMaxSteps];
 };
 
@@ -245,6 +250,50 @@ __global__ void __launch_bounds__(kThreads) k_cvt_tile(u64 *bits, CvtPlan P, int
     for (u64 w = threadIdx.x; w < tw; w += blockDim.x) g[w] = sm[w];
 }
 
+// A run of steps whose d are all multiples of a unit U (>= 4 words): every step
+// moves whole units, so the same step applies to each word column of the units
+// independently.  A block holds 2^wlog word columns of 2^slog consecutive
+// units (a segment-aligned range at least as long as the run's segments).
+__global__ void __launch_bounds__(kThreads) k_cvt_col(u64 *bits, CvtPlan P, int phase)
+{
+    extern __shared__ u64 sm[];
+    const int ulog = P.ulog[phase], wlog = P.wlog[phase], slog = P.slog[phase];
+    const u64 uw = 1ull << (ulog - 6);                  // words per unit
+    const u64 W = 1ull << wlog, S = 1ull << slog;
+    const u64 cols = uw >> wlog;                        // column blocks per unit
+    const u64 u0 = ((u64)blockIdx.x / cols) << slog, c0 = ((u64)blockIdx.x % cols) << wlog;
+    for (u64 k = threadIdx.x; k < S * W; k += blockDim.x)
+        sm[k] = bits[(u0 + (k >> wlog)) * uw + c0 + (k & (W - 1))];
+    __syncthreads();
+    const bool inverse = P.inverse != 0;
+    for (int s = P.first[phase]; s < P.first[phase] + P.count[phase]; ++s) {
+        const u64 H = P.h[s] >> ulog, D = P.d[s] >> ulog;      // in units
+        const int hl = __ffsll((long long)H) - 1;
+        // lo[q] ^= hi'[q - D], hi' = hi with the quotient fix (forward)
+        for (u64 k = threadIdx.x; k < (S / 2) * W; k += blockDim.x) {
+            const u64 e = k >> wlog, w = k & (W - 1);
+            const u64 base = (e >> hl) << (hl + 1), q = e & (H - 1);
+            if (q < D) continue;
+            const u64 r = q - D;
+            u64 hv = sm[((base + H + r) << wlog) + w];
+            if (!inverse && r < D) hv ^= sm[((base + 2 * H - D + r) << wlog) + w];
+            sm[((base + q) << wlog) + w] ^= hv;
+        }
+        __syncthreads();
+        // hi[r] ^= hi[H - D + r], r < D
+        const int dl = __ffsll((long long)D) - 1;
+        for (u64 k = threadIdx.x; k < (S >> (hl + 1)) * D * W; k += blockDim.x) {
+            const u64 w = k & (W - 1), rest = k >> wlog;
+            const u64 r = rest & (D - 1), seg = rest >> dl;
+            const u64 base = seg << (hl + 1);
+            sm[((base + H + r) << wlog) + w] ^= sm[((base + 2 * H - D + r) << wlog) + w];
+        }
+        __syncthreads();
+    }
+    for (u64 k = threadIdx.x; k < S * W; k += blockDim.x)
+        bits[(u0 + (k >> wlog)) * uw + c0 + (k & (W - 1))] = sm[k];
+}
+
 // Bounded-wait self-test: one block waits for a second arrival that never
 // comes, so the wait runs out and records GF2X_ETIMEOUT.
 __global__ void k_wait_timeout_probe(GridSync *gs, int *status, unsigned long long limit)
@@ -266,6 +315,7 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_
     if (inverse) std::vector<Step>(steps.rbegin(), steps.rend()).swap(steps);
     if (!g_configured) {
         cudaFuncSetAttribute(k_cvt_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
+        cudaFuncSetAttribute(k_cvt_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
         g_configured = true;
     }
 
@@ -276,29 +326,63 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_
     while ((1ull << tw_log) < P.words && tw_log < kTileWordsLog) ++tw_log;
     P.tw_log = tw_log;
     const u64 tile_bits = 64ull << tw_log;
+    const u64 tile_words = 1ull << kTileWordsLog;
+    // a column run with unit U and longest half H fits when each block can hold
+    // 4 words of 2H/U units (U >= 256 bits)
+    auto fits = [&](u64 U, u64 H) { return U >= 256 && 2 * H / U <= tile_words / 4 && 2 * H / U <= L / U; };
     P.nphase = 0;
-    for (size_t k = 0; k < steps.size(); ++k) {
-        P.h[k] = steps[k].h;
-        P.d[k] = steps[k].d;
-        const bool wide = 2 * steps[k].h > tile_bits;
-        if (wide || P.nphase == 0 || P.wide[P.nphase - 1]) {
-            P.wide[P.nphase] = wide ? 1 : 0;
-            P.first[P.nphase] = (unsigned char)k;
-            P.count[P.nphase] = 1;
-            ++P.nphase;
-        } else {
-            ++P.count[P.nphase - 1];
+    const size_t n = steps.size();
+    for (size_t k = 0; k < n; ++k) { P.h[k] = steps[k].h; P.d[k] = steps[k].d; }
+    for (size_t k = 0; k < n;) {
+        const int ph = P.nphase++;
+        P.first[ph] = (unsigned char)k;
+        if (2 * steps[k].h <= tile_bits) {              // run of in-tile steps
+            size_t j = k;
+            while (j < n && 2 * steps[j].h <= tile_bits && j - k < 255) ++j;
+            P.kind[ph] = PHASE_TILE;
+            P.count[ph] = (unsigned char)(j - k);
+            k = j;
+            continue;
+        }
+        u64 U = steps[k].d, H = steps[k].h;
+        size_t j = k + 1;
+        while (j < n) {
+            const u64 U2 = steps[j].d < U ? steps[j].d : U, H2 = steps[j].h > H ? steps[j].h : H;
+            if (!fits(U2, H2)) break;
+            U = U2; H = H2; ++j;
+        }
+        if (j - k >= 2 && fits(U, H)) {                 // column run
+            int ulog = 0, slog = 0;
+            while ((1ull << ulog) < U) ++ulog;
+            while ((1ull << slog) < 2 * H / U) ++slog;
+            int wlog = 2;                               // widest rows that still fit
+            while (wlog < 4 && (1ull << (wlog + 1)) <= (U >> 6) && ((2 * H / U) << (wlog + 1)) <= tile_words) ++wlog;
+            // as many units per block as fit (>= the run's segments)
+            while ((1ull << (slog + 1)) <= L / U && (1ull << (slog + 1 + wlog)) <= tile_words) ++slog;
+            P.kind[ph] = PHASE_COLUMN;
+            P.ulog[ph] = (unsigned char)ulog;
+            P.wlog[ph] = (unsigned char)wlog;
+            P.slog[ph] = (unsigned char)slog;
+            P.count[ph] = (unsigned char)(j - k);
+            k = j;
+        } else {                                        // one wide step
+            P.kind[ph] = PHASE_WIDE;
+            P.count[ph] = 1;
+            ++k;
         }
     }
     const u64 ntiles = P.words >> tw_log;
     const u64 wide_threads = P.words / 8;         // four lo words per thread
     for (int ph = 0; ph < P.nphase; ++ph) {
-        if (P.wide[ph]) {
+        if (P.kind[ph] == PHASE_WIDE) {
             const int s0 = P.first[ph];
             k_cvt_wide<<<(unsigned)((wide_threads + 255) / 256), 256, 0, st>>>(bits, P.words, P.h[s0], P.d[s0],
                                                                                 P.inverse);
-        } else {
+        } else if (P.kind[ph] == PHASE_TILE) {
             k_cvt_tile<<<(unsigned)ntiles, kThreads, (size_t)8 << tw_log, st>>>(bits, P, ph);
+        } else {
+            const u64 blocks = (P.words >> (P.ulog[ph] - 6 + P.slog[ph] - 0)) * ((1ull << (P.ulog[ph] - 6)) >> P.wlog[ph]);
+            k_cvt_col<<<(unsigned)blocks, kThreads, (size_t)8 << (P.slog[ph] + P.wlog[ph]), st>>>(bits, P, ph);
         }
         count_launch(ctx);
     }

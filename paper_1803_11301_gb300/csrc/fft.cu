@@ -6,7 +6,6 @@ namespace gf2x {
 namespace {
 
 constexpr int kCols = 32;            // word columns per Encode/Decode block
-constexpr int kPad = 65;             // padded row length of the Decode tile
 
 __device__ __forceinline__ void load_table(u64 *dst, const u64 *__restrict__ src)
 {
@@ -18,31 +17,65 @@ __device__ __forceinline__ void load_table(u64 *dst, const u64 *__restrict__ src
 // i.e. RW = n_p/64 words.  For the 64 points i in word column w, the 64 words
 // (row j, column w) form a 64x64 bit matrix whose transpose gives, per i, the
 // vector (a_{j n_p + i})_j; f_i = that vector times R (Alg. 4 lines 3-4).
-__global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, const u64 *__restrict__ enc,
-                                                u64 *__restrict__ f)
+//
+// A block stages 64 rows x 32 word columns in shared memory (coalesced row
+// reads); each warp transposes one column's 64x64 bit matrix with shuffles
+// (Sec. 4.4's block-swap transpose: a 32-bit half swap in registers, then
+// five exchange rounds across lanes) and applies R through 8-bit window tables
+// loaded once per block.  Rows at or above `rows` are zero and are not read.
+constexpr u64 kM16 = 0x0000FFFF0000FFFFull, kM8 = 0x00FF00FF00FF00FFull, kM4 = 0x0F0F0F0F0F0F0F0Full,
+              kM2 = 0x3333333333333333ull, kM1 = 0x5555555555555555ull;
+
+// Lane t holds rows t (A) and t + 32 (B) of a 64x64 bit matrix (bit c of row
+// r = M[r][c]); on return A = column t and B = column t + 32 (bit r = M[r][c]).
+// Applied to columns it returns rows.
+__device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
+{
+    const u64 a2 = (A & 0x00000000FFFFFFFFull) | (B << 32);
+    const u64 b2 = (A >> 32) | (B & 0xFFFFFFFF00000000ull);
+    A = a2;
+    B = b2;
+    const u64 masks[5] = {kM16, kM8, kM4, kM2, kM1};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const u64 m = masks[s];
+        const u64 ya = __shfl_xor_sync(0xffffffffu, A, j), yb = __shfl_xor_sync(0xffffffffu, B, j);
+        if (lane & j) {
+            A = ((ya & ~m) >> j) | (A & ~m);
+            B = ((yb & ~m) >> j) | (B & ~m);
+        } else {
+            A = (A & m) | ((ya & m) << j);
+            B = (B & m) | ((yb & m) << j);
+        }
+    }
+}
+
+constexpr int kPad = kCols + 1;      // padded row of the staging tile
+
+__global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, int rows,
+                                                const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups)
 {
     __shared__ u64 tab[8 * 256];
-    __shared__ u64 tile[64][kCols];
+    __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
-    const u64 w0 = (u64)blockIdx.x * cols;
-    load_table(tab, enc);
-    for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
-        int j = k / cols, w = k % cols;
-        tile[j][w] = novel[(u64)j * rw + w0 + w];
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int w = warp; w < cols; w += blockDim.x >> 5) {
-        u64 ulo = 0, uhi = 0;
-#pragma unroll 8
-        for (int j = 0; j < 64; ++j) {
-            u64 word = tile[j][w];
-            ulo |= ((word >> lane) & 1ull) << j;
-            uhi |= ((word >> (lane + 32)) & 1ull) << j;
+    load_table(tab, enc);
+    for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
+        const u64 w0 = g * cols;
+        __syncthreads();
+        for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
+            const int j = k / cols, w = k % cols;
+            tile[j * kPad + w] = j < rows ? novel[(u64)j * rw + w0 + w] : 0;
         }
-        u64 base = (w0 + w) * 64;
-        f[base + lane] = lin64(tab, ulo);
-        f[base + lane + 32] = lin64(tab, uhi);
+        __syncthreads();
+        for (int w = warp; w < cols; w += blockDim.x >> 5) {
+            u64 A = tile[lane * kPad + w], B = tile[(lane + 32) * kPad + w];
+            transpose64(A, B, lane);
+            const u64 base = (w0 + w) * 64;
+            f[base + lane] = lin64(tab, A);
+            f[base + lane + 32] = lin64(tab, B);
+        }
     }
 }
 
@@ -61,26 +94,32 @@ __global__ void k_encode_small(const u64 *__restrict__ novel, int l, const u64 *
 }
 
 // ------------------------------------------------------------------- Decode
+// The inverse of Encode: per point, the bits (c_{j n_p + i})_j = h_i R^{-1};
+// a warp transposes the 64 vectors of one word column back into 64 row words.
 __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 rw, const u64 *__restrict__ dec,
-                                                u64 *__restrict__ novel)
+                                                u64 *__restrict__ novel, u64 groups)
 {
     __shared__ u64 tab[8 * 256];
-    __shared__ u64 vec[kCols * kPad];
+    __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
-    const u64 w0 = (u64)blockIdx.x * cols;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     load_table(tab, dec);
     __syncthreads();
-    for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
-        int w = k >> 6, t = k & 63;
-        vec[w * kPad + t] = lin64(tab, h[(w0 + w) * 64 + t]);   // bit j = c_{j n_p + i}
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
-        int j = k / cols, w = k % cols;
-        u64 out = 0;
-#pragma unroll 8
-        for (int t = 0; t < 64; ++t) out |= ((vec[w * kPad + t] >> j) & 1ull) << t;
-        novel[(u64)j * rw + w0 + w] = out;
+    for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
+        const u64 w0 = g * cols;
+        for (int w = warp; w < cols; w += blockDim.x >> 5) {
+            const u64 base = (w0 + w) * 64;
+            u64 A = lin64(tab, h[base + lane]), B = lin64(tab, h[base + lane + 32]);
+            transpose64(A, B, lane);
+            tile[lane * kPad + w] = A;
+            tile[(lane + 32) * kPad + w] = B;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
+            const int j = k / cols, w = k % cols;
+            novel[(u64)j * rw + w0 + w] = tile[j * kPad + w];
+        }
+        __syncthreads();
     }
 }
 
@@ -127,14 +166,17 @@ inline unsigned blocks_for(u64 n, unsigned threads) { return (unsigned)((n + thr
 
 }  // namespace
 
-cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, cudaStream_t st)
+cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, cudaStream_t st)
 {
     if (l < 6) {
         k_encode_small<<<1, 64, 0, st>>>(novel, l, ctx->d_enc, f);
     } else {
-        u64 rw = 1ull << (l - 6);
-        u64 cols = rw < kCols ? rw : kCols;
-        k_encode<<<(unsigned)(rw / cols), 256, 0, st>>>(novel, rw, ctx->d_enc, f);
+        const u64 rw = 1ull << (l - 6), np = 1ull << l;
+        const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
+        int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
+        if (rows > 64) rows = 64;
+        const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        k_encode<<<(unsigned)grid, 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups);
     }
     count_launch(ctx);
     return cudaGetLastError();
@@ -145,9 +187,10 @@ cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t 
     if (l < 6) {
         k_decode_small<<<1, 64, 0, st>>>(h, l, ctx->d_dec, novel);
     } else {
-        u64 rw = 1ull << (l - 6);
-        u64 cols = rw < kCols ? rw : kCols;
-        k_decode<<<(unsigned)(rw / cols), 256, 0, st>>>(h, rw, ctx->d_dec, novel);
+        const u64 rw = 1ull << (l - 6);
+        const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
+        const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        k_decode<<<(unsigned)grid, 256, 0, st>>>(h, rw, ctx->d_dec, novel, groups);
     }
     count_launch(ctx);
     return cudaGetLastError();

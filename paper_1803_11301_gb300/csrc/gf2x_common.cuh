@@ -112,7 +112,7 @@ namespace gf2x {
 
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_t st);
 cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
-cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, cudaStream_t st);
+cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, cudaStream_t st);
 cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t st);
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st);
 cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, cudaStream_t st);
