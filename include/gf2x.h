@@ -131,6 +131,32 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
                                       const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                                       void *stream);
 
+/* One product of a batch: c = a * b, pointers and lengths as for gf2x_mul. */
+typedef struct gf2x_job {
+    const uint64_t *a;
+    uint64_t na_bits;
+    const uint64_t *b;
+    uint64_t nb_bits;
+    uint64_t *c;
+} gf2x_job;
+
+/* Device workspace for gf2x_mul_batch on these jobs (0 if a job is invalid
+ * or too long).  Depends on the lengths only. */
+GF2X_API size_t gf2x_batch_workspace_bytes(const gf2x_job *jobs, size_t count);
+
+/* Many independent products of uneven lengths in one call (Alg. 5 for each).
+ * The jobs are grouped by transform length n; every group runs the whole
+ * path with one launch per kernel for all its jobs (the kernels' second grid
+ * dimension is the job).  The host array `jobs` is read during the call and
+ * copied to the workspace; every device buffer follows the gf2x_mul rules
+ * (8-byte aligned, c disjoint from a, b and the workspace; jobs may share
+ * operands but not results).  Jobs with na or nb = 0 write nothing.
+ * Asynchronous.  From the second call with the same jobs (pointers and
+ * lengths) and workspace on, the kernels replay from a captured CUDA graph
+ * (at most 8 kept per context). */
+GF2X_API gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count,
+                                    void *workspace, size_t ws_bytes, void *stream);
+
 /* Self-test of the bounded device-side waits: launches one block that waits
  * on a grid barrier for an arrival that never comes.  The wait gives up after
  * a short limit (milliseconds), records GF2X_ETIMEOUT in the context status

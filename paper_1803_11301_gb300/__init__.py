@@ -40,6 +40,8 @@ ABI_FUNCTIONS = {
     "gf2x_host_workspace_bytes": (_SZ, [_U64, _U64]),
     "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_mul_noalloc": (_ST, [_P, _P, _U64, _P, _U64, _P, _P]),
+    "gf2x_batch_workspace_bytes": (_SZ, [_P, _SZ]),
+    "gf2x_mul_batch": (_ST, [_P, _P, _SZ, _P, _SZ, _P]),
     "gf2x_stream_status": (_ST, [_P, _P]),
     "gf2x_selftest_wait_timeout": (_ST, [_P, _P]),
     "gf2x_basis_cvt": (_ST, [_P, _P, _U64, _P]),
@@ -56,6 +58,12 @@ ABI_FUNCTIONS = {
 }
 
 _lib = None
+
+
+class Job(ctypes.Structure):
+    """gf2x_job: one product of a batch (device pointers and bit lengths)."""
+    _fields_ = [("a", ctypes.c_void_p), ("na_bits", ctypes.c_uint64), ("b", ctypes.c_void_p),
+                ("nb_bits", ctypes.c_uint64), ("c", ctypes.c_void_p)]
 
 
 class Gf2xError(RuntimeError):
@@ -215,6 +223,29 @@ class Context:
     def selftest_wait_timeout(self, stream=None):
         """Launch a bounded wait that must run out; the status word then reads GF2X_ETIMEOUT."""
         _check(self._lib.gf2x_selftest_wait_timeout(self._h, self._stream(stream)), "gf2x_selftest_wait_timeout")
+
+    def mul_batch(self, jobs, workspace=None, stream=None):
+        """Run many products in one call.  jobs: list of (a, na, b, nb, c) with CUDA tensors."""
+        arr = (Job * len(jobs))()
+        for k, (a, na, b, nb, c) in enumerate(jobs):
+            nc = product_bits(na, nb)
+            arr[k] = Job(self._tensor_ptr(a, _words(na), "a").value if na else a.data_ptr(), na,
+                         self._tensor_ptr(b, _words(nb), "b").value if nb else b.data_ptr(), nb,
+                         self._tensor_ptr(c, _words(nc), "c").value if nc else c.data_ptr())
+        need = int(self._lib.gf2x_batch_workspace_bytes(arr, len(jobs)))
+        if need == 0 and len(jobs):
+            raise Gf2xError(1, "gf2x_batch_workspace_bytes")
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_mul_batch(self._h, arr, len(jobs), ctypes.c_void_p(workspace.data_ptr()),
+                                        workspace.numel(), self._stream(stream)), "gf2x_mul_batch")
+        return [j[4] for j in jobs]
+
+    def batch_workspace_bytes(self, jobs) -> int:
+        arr = (Job * len(jobs))()
+        for k, (a, na, b, nb, c) in enumerate(jobs):
+            arr[k] = Job(a.data_ptr(), na, b.data_ptr(), nb, c.data_ptr())
+        return int(self._lib.gf2x_batch_workspace_bytes(arr, len(jobs)))
 
     def stream_status(self, stream=None) -> int:
         return int(self._lib.gf2x_stream_status(self._h, self._stream(stream)))

@@ -12,6 +12,7 @@
 //   top iButterfly layers of X; T <- Decode(X); iBasisCvt(T, n); c <- T (lines 8-10)
 // BasisCvt runs on L_a = max(64, next_pow2(na)) bits: the novelpoly basis
 // is triangular (deg X_k = k), so the coefficients at k >= L_a are zero.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -285,42 +286,80 @@ void destroy_entry(GraphEntry &g)
     }
 }
 
-// Lines 1-2 (or 4-5) of Alg. 5 for one operand: BasisCvt and Encode into F.
-gf2x_status forward(gf2x_ctx *ctx, const u64 *src, u64 nsrc, u64 n, u64 *T, u64 *F, cudaStream_t st)
+// One size class: `count` products with the same transform length n, whose
+// buffers X, Y, T (count x stride words each) hold the jobs one after
+// another.  Either a device job table (a batch) or direct pointers (count 1).
+struct ClassRun {
+    u64 n;
+    int count;
+    u64 La, Lb;                     // BasisCvt lengths (>= every operand of the class)
+    const JobDev *jobs;             // device job table, or null
+    const u64 *a, *b;               // direct operands when jobs is null
+    u64 na, nb;
+    u64 *c;
+    u64 max_c_words;                // longest product of the class, in words
+    u64 *X, *Y, *T;
+    u64 stride;                     // words between the buffers of consecutive jobs
+    bool square;                    // a == b (direct form only): one forward transform
+};
+
+// Lines 1-2 (or 4-5) of Alg. 5 for one operand of every job: load, BasisCvt, Encode.
+gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStream_t st)
 {
-    const int l = log2_u64(n) - 6;
-    u64 L = next_pow2(nsrc);
-    if (L < 64) L = 64;
-    { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, src, nsrc, T, n / 64, st)); }
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, st)); }
-    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, F, L, st)); }
+    const int l = log2_u64(r.n) - 6;
+    const u64 L = which ? r.Lb : r.La;
+    {
+        StageScope s(ctx, STAGE_LOAD, st);
+        if (r.jobs) TRY(gf2x::load_jobs(ctx, r.jobs, which, r.T, r.stride, r.n / 64, r.count, st));
+        else TRY(gf2x::load_bits(ctx, which ? r.b : r.a, which ? r.nb : r.na, r.T, r.n / 64, st));
+    }
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, st)); }
+    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, st)); }
+    return GF2X_OK;
+}
+
+gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
+{
+    const int l = log2_u64(r.n) - 6;
+    gf2x_status s = forward(ctx, r, 0, r.X, st);
+    if (s != GF2X_OK) return s;
+    if (!r.square) {
+        s = forward(ctx, r, 1, r.Y, st);
+        if (s != GF2X_OK) return s;
+    }
+    u64 *X = r.X, *Y = r.square ? nullptr : r.Y;
+    const int cnt = r.count;
+    const u64 sd = r.stride;
+    // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
+    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, X, Y, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, Y ? Y : X, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, r.T, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, st)); }
+    {
+        StageScope g(ctx, STAGE_STORE, st);
+        if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
+        else TRY(gf2x::store_bits(ctx, r.T, product_bits(r.na, r.nb), r.c, st));
+    }
     return GF2X_OK;
 }
 
 gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
                        cudaStream_t st)
 {
-    const u64 n = transform_bits(na, nb), nc = product_bits(na, nb);
-    const int l = log2_u64(n) - 6;
-    const size_t buf = buffer_bytes(n);
-    u64 *X = (u64 *)ws;
-    u64 *Y = (u64 *)((char *)ws + buf);
-    u64 *T = (u64 *)((char *)ws + 2 * buf);
-    gf2x_status s = forward(ctx, a, na, n, T, X, st);
-    if (s != GF2X_OK) return s;
-    const bool square = (a == b && na == nb);
-    if (!square) {
-        s = forward(ctx, b, nb, n, T, Y, st);
-        if (s != GF2X_OK) return s;
-    }
-    // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
-    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, X, square ? nullptr : Y, l, st)); }
-    { StageScope s(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, square ? X : Y, l, st)); }
-    { StageScope s(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, st)); }
-    { StageScope s(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, T, st)); }
-    { StageScope s(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, st)); }
-    { StageScope s(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, nc, c, st)); }
-    return GF2X_OK;
+    ClassRun r{};
+    r.n = transform_bits(na, nb);
+    r.count = 1;
+    r.La = next_pow2(na) < 64 ? 64 : next_pow2(na);
+    r.Lb = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
+    r.a = a; r.b = b; r.na = na; r.nb = nb; r.c = c;
+    const size_t buf = buffer_bytes(r.n);
+    r.X = (u64 *)ws;
+    r.Y = (u64 *)((char *)ws + buf);
+    r.T = (u64 *)((char *)ws + 2 * buf);
+    r.stride = 0;
+    r.square = (a == b && na == nb);
+    return run_class(ctx, r, st);
 }
 
 // gf2x_mul through the graph cache (falls back to direct launches while a key
@@ -406,6 +445,113 @@ gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
     return GF2X_OK;
 }
 
+// ---------------------------------------------------------------- batches
+constexpr int kMaxClassJobs = 16384;   // jobs per launch of one class (grid.y limit)
+
+struct BatchPlan {
+    std::vector<JobDev> table;          // jobs in class order (ascending n)
+    std::vector<ClassRun> runs;
+    size_t table_bytes = 0;
+    size_t total_bytes = 0;
+};
+
+// Group the non-empty jobs by transform length; lay out the workspace as
+// [job table][class 0: X, Y, T][class 1: ...] (256-byte aligned pieces).
+gf2x_status plan_batch(const gf2x_job *jobs, size_t count, BatchPlan &bp)
+{
+    std::vector<std::pair<u64, size_t>> order;
+    order.reserve(count);
+    for (size_t k = 0; k < count; ++k) {
+        const gf2x_job &j = jobs[k];
+        if (!product_bits(j.na_bits, j.nb_bits)) continue;
+        const u64 n = transform_bits(j.na_bits, j.nb_bits);
+        if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+        if (!j.a || !j.b || !j.c || !aligned8(j.a) || !aligned8(j.b) || !aligned8(j.c)) return GF2X_EINVAL;
+        const size_t cb = (size_t)((product_bits(j.na_bits, j.nb_bits) + 63) / 64) * 8;
+        if (overlap(j.c, cb, j.a, (size_t)((j.na_bits + 63) / 64) * 8) ||
+            overlap(j.c, cb, j.b, (size_t)((j.nb_bits + 63) / 64) * 8))
+            return GF2X_EINVAL;
+        order.push_back({n, k});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<u64, size_t> &x, const std::pair<u64, size_t> &y) { return x.first < y.first; });
+    bp.table.clear();
+    bp.runs.clear();
+    for (auto &o : order) {
+        const gf2x_job &j = jobs[o.second];
+        bp.table.push_back(JobDev{j.a, j.na_bits, j.b, j.nb_bits, j.c, 0});
+    }
+    bp.table_bytes = round_up(bp.table.size() * sizeof(JobDev));
+    size_t off = bp.table_bytes;
+    for (size_t k = 0; k < order.size();) {
+        size_t e = k;
+        while (e < order.size() && order[e].first == order[k].first && (int)(e - k) < kMaxClassJobs) ++e;
+        ClassRun r{};
+        r.n = order[k].first;
+        r.count = (int)(e - k);
+        u64 ma = 0, mb = 0, mc = 0;
+        for (size_t t = k; t < e; ++t) {
+            const JobDev &jd = bp.table[t];
+            ma = jd.na > ma ? jd.na : ma;
+            mb = jd.nb > mb ? jd.nb : mb;
+            const u64 cw = (product_bits(jd.na, jd.nb) + 63) / 64;
+            mc = cw > mc ? cw : mc;
+        }
+        r.La = next_pow2(ma) < 64 ? 64 : next_pow2(ma);
+        r.Lb = next_pow2(mb) < 64 ? 64 : next_pow2(mb);
+        r.max_c_words = mc;
+        r.stride = buffer_bytes(r.n) / 8;
+        r.jobs = (const JobDev *)(uintptr_t)k;          // index for now; made a pointer per call
+        const size_t region = (size_t)r.count * buffer_bytes(r.n);
+        r.X = (u64 *)(uintptr_t)off;
+        r.Y = (u64 *)(uintptr_t)(off + region);
+        r.T = (u64 *)(uintptr_t)(off + 2 * region);
+        off += 3 * region;
+        bp.runs.push_back(r);
+        k = e;
+    }
+    bp.total_bytes = off;
+    return GF2X_OK;
+}
+
+// The runs of a plan with the workspace base applied.
+std::vector<ClassRun> bind_runs(const BatchPlan &bp, void *ws)
+{
+    std::vector<ClassRun> out = bp.runs;
+    char *base = (char *)ws;
+    for (ClassRun &r : out) {
+        r.jobs = (const JobDev *)(base) + (uintptr_t)r.jobs;
+        r.X = (u64 *)(base + (uintptr_t)r.X);
+        r.Y = (u64 *)(base + (uintptr_t)r.Y);
+        r.T = (u64 *)(base + (uintptr_t)r.T);
+    }
+    return out;
+}
+
+u64 hash_table(const std::vector<JobDev> &t, const void *ws)
+{
+    u64 h = 1469598103934665603ull ^ (u64)(uintptr_t)ws;
+    const unsigned char *p = (const unsigned char *)t.data();
+    for (size_t k = 0; k < t.size() * sizeof(JobDev); ++k) h = (h ^ p[k]) * 1099511628211ull;
+    return h ^ (u64)t.size();
+}
+
+struct BatchGraph {
+    u64 key;
+    bool profiling;
+    cudaGraphExec_t exec;
+    unsigned long long launches[STAGE_COUNT];
+    std::vector<Rec> recs;
+    unsigned long long stamp;
+};
+
+struct BatchCache {
+    std::vector<BatchGraph> entries;
+    std::vector<u64> seen;
+};
+
+constexpr size_t kMaxBatchGraphs = 8;
+
 bool valid_n(u64 n) { return n >= 64 && n <= kMaxTransformBits && (n & (n - 1)) == 0; }
 
 }  // namespace
@@ -442,9 +588,11 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     ctx->device = device;
     ctx->prof = new (std::nothrow) Profiler();
     ctx->graphs = new (std::nothrow) GraphCache();
-    if (!ctx->prof || !ctx->graphs) {
+    ctx->batch_graphs = new (std::nothrow) BatchCache();
+    if (!ctx->prof || !ctx->graphs || !ctx->batch_graphs) {
         delete profiler(ctx);
         delete graphs(ctx);
+        delete (BatchCache *)ctx->batch_graphs;
         delete ctx;
         return GF2X_ENOMEM;
     }
@@ -452,7 +600,13 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
 
     u64 v[64];
-    auto fail = [&](gf2x_status st) { delete profiler(ctx); delete graphs(ctx); delete ctx; return st; };
+    auto fail = [&](gf2x_status st) {
+        delete profiler(ctx);
+        delete graphs(ctx);
+        delete (BatchCache *)ctx->batch_graphs;
+        delete ctx;
+        return st;
+    };
     if (!cantor_basis(v)) return fail(GF2X_EINVAL);
     std::memcpy(ctx->cantor, v, sizeof v);
 
@@ -498,6 +652,13 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx)
 {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    if (BatchCache *bc = (BatchCache *)ctx->batch_graphs) {
+        for (BatchGraph &e : bc->entries) {
+            cudaGraphExecDestroy(e.exec);
+            for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        }
+        delete bc;
+    }
     if (GraphCache *gc = graphs(ctx)) {
         for (GraphEntry &e : gc->entries) destroy_entry(e);
         if (gc->cap) cudaStreamDestroy(gc->cap);
@@ -603,7 +764,7 @@ gf2x_status gf2x_basis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stre
     if (!valid_n(L)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_BASISCVT, (cudaStream_t)stream);
-    return from_cuda(gf2x::basis_cvt(ctx, bits, L, false, (cudaStream_t)stream));
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, false, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stream)
@@ -613,7 +774,7 @@ gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *str
     if (!valid_n(L)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_IBASISCVT, (cudaStream_t)stream);
-    return from_cuda(gf2x::basis_cvt(ctx, bits, L, true, (cudaStream_t)stream));
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, true, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64_t *f, void *stream)
@@ -623,7 +784,7 @@ gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64
     if (!valid_n(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
-    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, n, (cudaStream_t)stream));
+    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, n, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)
@@ -633,7 +794,7 @@ gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *
     if (!valid_n(n) || overlap(novel, n / 8, h, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_DECODE, (cudaStream_t)stream);
-    return from_cuda(gf2x::decode(ctx, h, log2_u64(n) - 6, novel, (cudaStream_t)stream));
+    return from_cuda(gf2x::decode(ctx, h, log2_u64(n) - 6, novel, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
@@ -643,7 +804,7 @@ gf2x_status gf2x_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
     if (!valid_n(n)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_BUTTERFLY, (cudaStream_t)stream);
-    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, false, (cudaStream_t)stream));
+    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, false, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
@@ -653,7 +814,7 @@ gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream
     if (!valid_n(n)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_IBUTTERFLY, (cudaStream_t)stream);
-    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, true, (cudaStream_t)stream));
+    return from_cuda(gf2x::butterfly(ctx, f, log2_u64(n) - 6, true, 1, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint64_t count,
@@ -672,6 +833,109 @@ gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream)
     if (!ctx) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     return from_cuda(gf2x::wait_timeout_probe(ctx, ctx->d_sync, (cudaStream_t)stream));
+}
+
+size_t gf2x_batch_workspace_bytes(const gf2x_job *jobs, size_t count)
+{
+    if (!jobs && count) return 0;
+    BatchPlan bp;
+    if (plan_batch(jobs, count, bp) != GF2X_OK) return 0;
+    return bp.total_bytes + kAlign;
+}
+
+gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx || (!jobs && count)) return GF2X_EINVAL;
+    BatchPlan bp;
+    gf2x_status s = plan_batch(jobs, count, bp);
+    if (s != GF2X_OK) return s;
+    if (bp.table.empty()) return GF2X_OK;
+    if (!ws || ((uintptr_t)ws % kAlign)) return GF2X_EINVAL;
+    if (ws_bytes < bp.total_bytes + kAlign) return GF2X_ENOSPACE;
+    for (const JobDev &j : bp.table)
+        if (overlap(j.c, (size_t)((product_bits(j.na, j.nb) + 63) / 64) * 8, ws, bp.total_bytes)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the job table goes to the device before the kernels (every call)
+    TRY(cudaMemcpyAsync(ws, bp.table.data(), bp.table.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
+    const std::vector<ClassRun> runs = bind_runs(bp, ws);
+    auto run_all = [&](cudaStream_t s2) -> gf2x_status {
+        for (const ClassRun &r : runs) {
+            gf2x_status e = run_class(ctx, r, s2);
+            if (e != GF2X_OK) return e;
+        }
+        return GF2X_OK;
+    };
+    // graph cache, keyed by the job table and the workspace (second call captures)
+    BatchCache *bc = (BatchCache *)ctx->batch_graphs;
+    GraphCache *gc = graphs(ctx);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (gc->disabled || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return run_all(st);
+    const u64 key = hash_table(bp.table, ws);
+    for (BatchGraph &e : bc->entries)
+        if (e.key == key && e.profiling == ctx->profiling) {
+            e.stamp = ++gc->clock;
+            TRY(cudaGraphLaunch(e.exec, st));
+            for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
+            if (ctx->profiling)
+                for (const Rec &r : e.recs) profiler(ctx)->pending.push_back(r);
+            return GF2X_OK;
+        }
+    bool repeat = false;
+    for (size_t k = 0; k < bc->seen.size(); ++k)
+        if (bc->seen[k] == key) {
+            repeat = true;
+            bc->seen.erase(bc->seen.begin() + (long)k);
+            break;
+        }
+    if (!repeat) {
+        if (bc->seen.size() >= 32) bc->seen.erase(bc->seen.begin());
+        bc->seen.push_back(key);
+        return run_all(st);
+    }
+    if (!gc->cap && cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking) != cudaSuccess) return run_all(st);
+    BatchGraph e{};
+    e.key = key;
+    e.profiling = ctx->profiling;
+    unsigned long long before[STAGE_COUNT];
+    for (int k = 0; k < STAGE_COUNT; ++k) before[k] = ctx->launches[k];
+    Profiler *p = profiler(ctx);
+    if (cudaStreamBeginCapture(gc->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return run_all(st);
+    p->capture = &e.recs;
+    s = run_all(gc->cap);
+    p->capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(gc->cap, &graph);
+    for (int k = 0; k < STAGE_COUNT; ++k) {
+        e.launches[k] = ctx->launches[k] - before[k];
+        ctx->launches[k] = before[k];
+    }
+    if (s != GF2X_OK || ce != cudaSuccess || !graph ||
+        (cudaGraphInstantiate(&e.exec, graph, 0) != cudaSuccess)) {
+        if (graph) cudaGraphDestroy(graph);
+        for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        cudaGetLastError();
+        return s != GF2X_OK ? s : run_all(st);
+    }
+    cudaGraphDestroy(graph);
+    if (bc->entries.size() >= kMaxBatchGraphs) {
+        size_t old = 0;
+        for (size_t k = 1; k < bc->entries.size(); ++k)
+            if (bc->entries[k].stamp < bc->entries[old].stamp) old = k;
+        cudaGraphExecDestroy(bc->entries[old].exec);
+        for (Rec &r : bc->entries[old].recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        bc->entries.erase(bc->entries.begin() + (long)old);
+    }
+    e.stamp = ++gc->clock;
+    bc->entries.push_back(e);
+    BatchGraph &ent = bc->entries.back();
+    TRY(cudaGraphLaunch(ent.exec, st));
+    for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += ent.launches[k];
+    if (ctx->profiling)
+        for (const Rec &r : ent.recs) p->pending.push_back(r);
+    return GF2X_OK;
 }
 
 const char *gf2x_stage_name(int stage)

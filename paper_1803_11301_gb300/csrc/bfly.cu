@@ -99,11 +99,14 @@ __device__ __forceinline__ u64 cantor(const u64 *__restrict__ cvt, u64 u)
 // 2^(M-1-r) - 1 on; table j of that layer serves rows u with u >> (r+1) = j.
 template <int M, bool INV>
 __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
-                                                       const u64 *__restrict__ cvt, const u64 *__restrict__ vb)
+                                                       const u64 *__restrict__ cvt, const u64 *__restrict__ vb,
+                                                       int arrays, u64 stride)
 {
     extern __shared__ u64 tabs[];
     constexpr int ntab = (1 << M) - 1;
-    u64 *x = blockIdx.y ? x1 : x0;
+    // blockIdx.y = job * arrays + array; jobs of a batch are `stride` words apart
+    const u64 job = blockIdx.y / arrays;
+    u64 *x = ((blockIdx.y % arrays) ? x1 : x0) + job * stride;
     const u64 first = (u64)blockIdx.x * per_block;
     const u64 group = first / chunks;
     build_tables(tabs, ntab, [&](int t) {
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
         const u64 blk = (group << lvl) | (u64)j;        // block index at layer p + r
         return vb[l + 32 - (p + r)] ^ cantor(cvt, blk << 1);
     });
-    const u64 stride = 1ull << p;
+    const u64 rstride = 1ull << p;                      // distance between the rows of a column
     for (int ch = 0; ch < per_block; ++ch) {
         const u64 chunk = first + ch;
         if (chunk / chunks != group) break;
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
         const u64 base = (group << (p + M)) + col;
         u64 v[1 << M];
 #pragma unroll
-        for (int u = 0; u < (1 << M); ++u) v[u] = x[base + (u64)u * stride];
+        for (int u = 0; u < (1 << M); ++u) v[u] = x[base + (u64)u * rstride];
 #pragma unroll
         for (int s2 = 0; s2 < M; ++s2) {
             const int r = INV ? s2 : M - 1 - s2;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
             }
         }
 #pragma unroll
-        for (int u = 0; u < (1 << M); ++u) x[base + (u64)u * stride] = v[u];
+        for (int u = 0; u < (1 << M); ++u) x[base + (u64)u * rstride] = v[u];
     }
 }
 
@@ -210,9 +213,11 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
 }
 
 __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
-                                                          const u64 *__restrict__ vb, int mode)
+                                                          const u64 *__restrict__ vb, int mode, u64 stride)
 {
     extern __shared__ u64 sm[];
+    X += (u64)blockIdx.y * stride;                      // job of a batch
+    if (Y) Y += (u64)blockIdx.y * stride;
     const int T = 1 << bt;
     const bool fused = mode == BOTTOM_FUSED;
     u64 *a = sm;
@@ -261,13 +266,14 @@ size_t bottom_smem(int bt, bool fused)
 
 template <int M, bool INV>
 void launch_top(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
-                const u64 *cvt, const u64 *vb)
+                const u64 *cvt, const u64 *vb, int arrays, u64 stride)
 {
     size_t smem = (size_t)((1 << M) - 1) * kTab * sizeof(u64);
-    k_bfly_top<M, INV><<<grid, kThreads, smem, st>>>(x0, x1, l, p, chunks, per_block, cvt, vb);
+    k_bfly_top<M, INV><<<grid, kThreads, smem, st>>>(x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride);
 }
 
-cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, cudaStream_t st)
+cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, int count, u64 stride,
+                       cudaStream_t st)
 {
     // passes over layers [bt, l) in groups of <= kTopLayers; high to low for the forward transform
     const int npass = (l - bt + kTopLayers - 1) / kTopLayers;
@@ -279,21 +285,21 @@ cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inve
         const u64 groups = (1ull << l) >> (p + m);
         // chunks per block: up to 8 (tables built once per block), but keep at
         // least two blocks per SM; a power of two, so it divides `chunks`
-        const u64 arrays = x1 ? 2 : 1;
-        u64 pb = chunks * groups * arrays / (2 * (u64)ctx->num_sms);
+        const int arrays = x1 ? 2 : 1;
+        u64 pb = chunks * groups * (u64)arrays * (u64)count / (2 * (u64)ctx->num_sms);
         int per_block = 1;
         while (per_block < 8 && (u64)(2 * per_block) <= pb && (u64)(2 * per_block) <= chunks) per_block *= 2;
-        dim3 grid((unsigned)(chunks * groups / per_block), (unsigned)arrays);
+        dim3 grid((unsigned)(chunks * groups / per_block), (unsigned)(arrays * count));
         const u64 *cvt = ctx->d_cvt, *vb = ctx->d_cantor;
         switch (m * 2 + (inverse ? 1 : 0)) {
-        case 2: launch_top<1, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 3: launch_top<1, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 4: launch_top<2, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 5: launch_top<2, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 6: launch_top<3, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 7: launch_top<3, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        case 8: launch_top<4, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
-        default: launch_top<4, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb); break;
+        case 2: launch_top<1, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 3: launch_top<1, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 4: launch_top<2, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 5: launch_top<2, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 6: launch_top<3, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 7: launch_top<3, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 8: launch_top<4, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        default: launch_top<4, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
         }
         count_launch(ctx);
     }
@@ -311,50 +317,51 @@ void configure()
 
 }  // namespace
 
-// Forward (or inverse) Butterfly of one transform of 2^l points.
-cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st)
+// Forward (or inverse) Butterfly of `count` transforms of 2^l points each,
+// `stride` words apart.
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
     if (!inverse) {
-        cudaError_t e = top_passes(ctx, x, nullptr, l, bt, false, st);
+        cudaError_t e = top_passes(ctx, x, nullptr, l, bt, false, count, stride, st);
         if (e != cudaSuccess) return e;
     }
     if (bt > 0) {
-        k_bfly_bottom<<<(unsigned)(1ull << (l - bt)), kThreads, bottom_smem(bt, false), st>>>(
-            x, nullptr, l, bt, ctx->d_cvt, ctx->d_cantor, inverse ? BOTTOM_INV : BOTTOM_FWD);
+        k_bfly_bottom<<<dim3((unsigned)(1ull << (l - bt)), count), kThreads, bottom_smem(bt, false), st>>>(
+            x, nullptr, l, bt, ctx->d_cvt, ctx->d_cantor, inverse ? BOTTOM_INV : BOTTOM_FWD, stride);
         count_launch(ctx);
     }
-    if (inverse) return top_passes(ctx, x, nullptr, l, bt, true, st);
+    if (inverse) return top_passes(ctx, x, nullptr, l, bt, true, count, stride, st);
     return cudaGetLastError();
 }
 
-// The top layers of both forward transforms in one launch per pass.
-cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, cudaStream_t st)
+// The top layers of both forward transforms (X and Y, or X alone) in one launch per pass.
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    return top_passes(ctx, x0, x1, l, bt, false, st);
+    return top_passes(ctx, x0, x1, l, bt, false, count, stride, st);
 }
 
 // Bottom layers of both forward transforms, the pointwise product and the
 // bottom layers of the inverse: X <- low layers of iButterfly(fwd(X) * fwd(Y)).
-cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, cudaStream_t st)
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    k_bfly_bottom<<<(unsigned)(1ull << (l - bt)), kThreads, bottom_smem(bt, true), st>>>(X, Y, l, bt, ctx->d_cvt,
-                                                                                         ctx->d_cantor, BOTTOM_FUSED);
+    k_bfly_bottom<<<dim3((unsigned)(1ull << (l - bt)), count), kThreads, bottom_smem(bt, true), st>>>(
+        X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, BOTTOM_FUSED, stride);
     count_launch(ctx);
     return cudaGetLastError();
 }
 
 // The top layers of the inverse.
-cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, cudaStream_t st)
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    return top_passes(ctx, x, nullptr, l, bt, true, st);
+    return top_passes(ctx, x, nullptr, l, bt, true, count, stride, st);
 }
 
 }  // namespace gf2x

@@ -190,8 +190,9 @@ __device__ void tile_run(u64 *sm, u64 tw, const CvtPlan &P, int first, int count
 
 // One wide step in place (segments larger than a tile, so h >= 2^18 bits, hw >= 4096 words).
 // Each thread owns four consecutive lo words.
-__global__ void __launch_bounds__(256) k_cvt_wide(u64 *bits, u64 words, u64 h, u64 d, int inverse)
+__global__ void __launch_bounds__(256) k_cvt_wide(u64 *bits, u64 words, u64 h, u64 d, int inverse, u64 stride)
 {
+    bits += (u64)blockIdx.y * stride;             // job of a batch
     const u64 hw = h >> 6;
     const int hl = __ffsll((long long)hw) - 1;
     const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,9 +240,10 @@ __global__ void __launch_bounds__(256) k_cvt_wide(u64 *bits, u64 words, u64 h, u
 }
 
 // A run of tile steps: one block per tile of 2^tw_log words.
-__global__ void __launch_bounds__(kThreads) k_cvt_tile(u64 *bits, CvtPlan P, int phase)
+__global__ void __launch_bounds__(kThreads) k_cvt_tile(u64 *bits, CvtPlan P, int phase, u64 stride)
 {
     extern __shared__ u64 sm[];
+    bits += (u64)blockIdx.y * stride;
     const u64 tw = 1ull << P.tw_log;
     u64 *g = bits + (u64)blockIdx.x * tw;
     for (u64 w = threadIdx.x; w < tw; w += blockDim.x) sm[w] = g[w];
@@ -254,9 +256,10 @@ __global__ void __launch_bounds__(kThreads) k_cvt_tile(u64 *bits, CvtPlan P, int
 // moves whole units, so the same step applies to each word column of the units
 // independently.  A block holds 2^wlog word columns of 2^slog consecutive
 // units (a segment-aligned range at least as long as the run's segments).
-__global__ void __launch_bounds__(kThreads) k_cvt_col(u64 *bits, CvtPlan P, int phase)
+__global__ void __launch_bounds__(kThreads) k_cvt_col(u64 *bits, CvtPlan P, int phase, u64 stride)
 {
     extern __shared__ u64 sm[];
+    bits += (u64)blockIdx.y * stride;
     const int ulog = P.ulog[phase], wlog = P.wlog[phase], slog = P.slog[phase];
     const u64 uw = 1ull << (ulog - 6);                  // words per unit
     const u64 W = 1ull << wlog, S = 1ull << slog;
@@ -305,7 +308,7 @@ bool g_configured = false;
 
 }  // namespace
 
-cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_t st)
+cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st)
 {
     int K = 0;
     while ((1ull << K) < L) ++K;
@@ -376,13 +379,14 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_
     for (int ph = 0; ph < P.nphase; ++ph) {
         if (P.kind[ph] == PHASE_WIDE) {
             const int s0 = P.first[ph];
-            k_cvt_wide<<<(unsigned)((wide_threads + 255) / 256), 256, 0, st>>>(bits, P.words, P.h[s0], P.d[s0],
-                                                                                P.inverse);
+            k_cvt_wide<<<dim3((unsigned)((wide_threads + 255) / 256), count), 256, 0, st>>>(bits, P.words, P.h[s0],
+                                                                                          P.d[s0], P.inverse, stride);
         } else if (P.kind[ph] == PHASE_TILE) {
-            k_cvt_tile<<<(unsigned)ntiles, kThreads, (size_t)8 << tw_log, st>>>(bits, P, ph);
+            k_cvt_tile<<<dim3((unsigned)ntiles, count), kThreads, (size_t)8 << tw_log, st>>>(bits, P, ph, stride);
         } else {
             const u64 blocks = (P.words >> (P.ulog[ph] - 6 + P.slog[ph] - 0)) * ((1ull << (P.ulog[ph] - 6)) >> P.wlog[ph]);
-            k_cvt_col<<<(unsigned)blocks, kThreads, (size_t)8 << (P.slog[ph] + P.wlog[ph]), st>>>(bits, P, ph);
+            k_cvt_col<<<dim3((unsigned)blocks, count), kThreads, (size_t)8 << (P.slog[ph] + P.wlog[ph]), st>>>(bits, P, ph,
+                                                                                                         stride);
         }
         count_launch(ctx);
     }

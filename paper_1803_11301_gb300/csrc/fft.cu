@@ -54,8 +54,10 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
 constexpr int kPad = kCols + 1;      // padded row of the staging tile
 
 __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, int rows,
-                                                const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups)
+                                                const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups, u64 stride)
 {
+    novel += (u64)blockIdx.y * stride;            // job of a batch
+    f += (u64)blockIdx.y * stride;
     __shared__ u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
@@ -80,8 +82,11 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
 }
 
 // n_p < 64: the whole transform is at most 32 words; one block, bit by bit.
-__global__ void k_encode_small(const u64 *__restrict__ novel, int l, const u64 *__restrict__ enc, u64 *__restrict__ f)
+__global__ void k_encode_small(const u64 *__restrict__ novel, int l, const u64 *__restrict__ enc, u64 *__restrict__ f,
+                               u64 stride)
 {
+    novel += (u64)blockIdx.y * stride;
+    f += (u64)blockIdx.y * stride;
     const u64 np = 1ull << l;
     for (u64 i = threadIdx.x; i < np; i += blockDim.x) {
         u64 u = 0;
@@ -97,8 +102,10 @@ __global__ void k_encode_small(const u64 *__restrict__ novel, int l, const u64 *
 // The inverse of Encode: per point, the bits (c_{j n_p + i})_j = h_i R^{-1};
 // a warp transposes the 64 vectors of one word column back into 64 row words.
 __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 rw, const u64 *__restrict__ dec,
-                                                u64 *__restrict__ novel, u64 groups)
+                                                u64 *__restrict__ novel, u64 groups, u64 stride)
 {
+    h += (u64)blockIdx.y * stride;
+    novel += (u64)blockIdx.y * stride;
     __shared__ u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
@@ -123,8 +130,11 @@ __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 r
     }
 }
 
-__global__ void k_decode_small(const u64 *__restrict__ h, int l, const u64 *__restrict__ dec, u64 *__restrict__ novel)
+__global__ void k_decode_small(const u64 *__restrict__ h, int l, const u64 *__restrict__ dec, u64 *__restrict__ novel,
+                               u64 stride)
 {
+    h += (u64)blockIdx.y * stride;
+    novel += (u64)blockIdx.y * stride;
     __shared__ u64 vec[64];
     const u64 np = 1ull << l;
     for (u64 i = threadIdx.x; i < np; i += blockDim.x) vec[i] = lin64(dec, h[i]);
@@ -162,35 +172,69 @@ __global__ void k_load_bits(const u64 *__restrict__ src, u64 nbits, u64 *__restr
     dst[w] = v;
 }
 
+// Batch forms: job j of the launch (blockIdx.y) reads operand `which` of
+// jobs[j] into dst + j * stride, or writes its product from src + j * stride.
+__global__ void k_load_jobs(const JobDev *__restrict__ jobs, int which, u64 *__restrict__ dst, u64 stride,
+                            u64 dst_words)
+{
+    const JobDev jb = jobs[blockIdx.y];
+    const u64 *src = which ? jb.b : jb.a;
+    const u64 nbits = which ? jb.nb : jb.na;
+    dst += (u64)blockIdx.y * stride;
+    for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < dst_words; w += (u64)gridDim.x * blockDim.x) {
+        const u64 nw = (nbits + 63) >> 6;
+        u64 v = 0;
+        if (w < nw) {
+            v = src[w];
+            if (w == nw - 1 && (nbits & 63)) v &= (~0ull) >> (64 - (nbits & 63));
+        }
+        dst[w] = v;
+    }
+}
+
+__global__ void k_store_jobs(const u64 *__restrict__ src, u64 stride, const JobDev *__restrict__ jobs)
+{
+    const JobDev jb = jobs[blockIdx.y];
+    const u64 nc = (jb.na && jb.nb) ? jb.na + jb.nb - 1 : 0;
+    const u64 nw = (nc + 63) >> 6;
+    src += (u64)blockIdx.y * stride;
+    for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x) {
+        u64 v = src[w];
+        if (w == nw - 1 && (nc & 63)) v &= (~0ull) >> (64 - (nc & 63));
+        jb.c[w] = v;
+    }
+}
+
 inline unsigned blocks_for(u64 n, unsigned threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
-cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, cudaStream_t st)
+cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
+                   cudaStream_t st)
 {
     if (l < 6) {
-        k_encode_small<<<1, 64, 0, st>>>(novel, l, ctx->d_enc, f);
+        k_encode_small<<<dim3(1, count), 64, 0, st>>>(novel, l, ctx->d_enc, f, stride);
     } else {
         const u64 rw = 1ull << (l - 6), np = 1ull << l;
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
         if (rows > 64) rows = 64;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
-        k_encode<<<(unsigned)grid, 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups);
+        k_encode<<<dim3((unsigned)grid, count), 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups, stride);
     }
     count_launch(ctx);
     return cudaGetLastError();
 }
 
-cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t st)
+cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st)
 {
     if (l < 6) {
-        k_decode_small<<<1, 64, 0, st>>>(h, l, ctx->d_dec, novel);
+        k_decode_small<<<dim3(1, count), 64, 0, st>>>(h, l, ctx->d_dec, novel, stride);
     } else {
         const u64 rw = 1ull << (l - 6);
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
-        k_decode<<<(unsigned)grid, 256, 0, st>>>(h, rw, ctx->d_dec, novel, groups);
+        k_decode<<<dim3((unsigned)grid, count), 256, 0, st>>>(h, rw, ctx->d_dec, novel, groups, stride);
     }
     count_launch(ctx);
     return cudaGetLastError();
@@ -221,6 +265,28 @@ cudaError_t store_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, cudaS
         k_load_bits<<<blocks_for(nw, 256), 256, 0, st>>>(src, nbits, dst, nw);
         count_launch(ctx);
     }
+    return cudaGetLastError();
+}
+
+}  // namespace gf2x
+
+namespace gf2x {
+
+cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u64 stride, u64 dst_words, int count,
+                      cudaStream_t st)
+{
+    const u64 b = (dst_words + 255) / 256;
+    k_load_jobs<<<dim3((unsigned)(b < 1024 ? b : 1024), count), 256, 0, st>>>(jobs, which, dst, stride, dst_words);
+    count_launch(ctx);
+    return cudaGetLastError();
+}
+
+cudaError_t store_jobs(gf2x_ctx *ctx, const u64 *src, u64 stride, const JobDev *jobs, u64 max_words, int count,
+                       cudaStream_t st)
+{
+    const u64 b = (max_words + 255) / 256;
+    k_store_jobs<<<dim3((unsigned)(b < 1024 ? (b ? b : 1) : 1024), count), 256, 0, st>>>(src, stride, jobs);
+    count_launch(ctx);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,17 @@ __device__ __forceinline__ u64 lin64(const u64 *__restrict__ t, u64 x)
     return r;
 }
 
+// One product of a batch as the device sees it (the job table lives in the
+// workspace).  nc = na + nb - 1 bits (0 if either is 0).
+struct JobDev {
+    const u64 *a;
+    u64 na;
+    const u64 *b;
+    u64 nb;
+    u64 *c;
+    u64 pad;
+};
+
 // State of one grid-wide barrier (see cvt.cu); must be zero before a launch.
 struct GridSync {
     unsigned count;   // blocks arrived in the current generation
@@ -101,6 +112,7 @@ struct gf2x_ctx {
     bool profiling;
     void *prof;                         // event pool, see api.cu
     void *graphs;                       // CUDA graph cache of gf2x_mul, see api.cu
+    void *batch_graphs;                 // CUDA graph cache of gf2x_mul_batch
 };
 
 // Count one kernel launch against the current stage.
@@ -110,14 +122,21 @@ inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] +
 // All enqueue on `st` and return cudaGetLastError().
 namespace gf2x {
 
-cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, cudaStream_t st);
+// Batched forms: `count` jobs whose buffers are `stride` words apart
+// (count = 1, stride = 0 for a single product).
+cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
 cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
-cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, cudaStream_t st);
-cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, cudaStream_t st);
-cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, cudaStream_t st);
-cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, cudaStream_t st);
-cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, cudaStream_t st);
-cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, cudaStream_t st);
+cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
+                   cudaStream_t st);
+cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st);
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st);
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u64 stride, u64 dst_words, int count,
+                      cudaStream_t st);
+cudaError_t store_jobs(gf2x_ctx *ctx, const u64 *src, u64 stride, const JobDev *jobs, u64 max_words, int count,
+                       cudaStream_t st);
 cudaError_t pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
 cudaError_t load_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, u64 dst_words, cudaStream_t st);
 cudaError_t store_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, cudaStream_t st);

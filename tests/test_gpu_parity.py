@@ -240,3 +240,56 @@ def test_argument_errors(ctx):
     with pytest.raises(Gf2xError):
         ctx.encode(a, 100)
     assert ctx.stream_status() == 0
+
+
+# ---------------------------------------------------------------- batches
+def _batch_jobs(ctx, lengths, seed):
+    import torch
+    jobs, host = [], []
+    for k, (na, nb) in enumerate(lengths):
+        a = synth.operand(synth.config_seed(seed, 2 * k), max(na, 1))
+        b = synth.operand(synth.config_seed(seed, 2 * k + 1), max(nb, 1))
+        da, db = dev(a), dev(b)
+        nc = na + nb - 1 if na and nb else 0
+        c = torch.full((max((nc + 63) // 64, 1),), -1, dtype=torch.int64, device="cuda")
+        jobs.append((da, na, db, nb, c))
+        host.append((a, b))
+    return jobs, host
+
+
+def test_batch_uneven_lengths_bit_exact(ctx):
+    lens = synth.loguniform_lengths(synth.config_seed(4, 7), 400, 6.0, 17.0).reshape(200, 2)
+    lengths = [(int(x), int(y)) for x, y in lens] + [(0, 100), (100, 0), (1, 1), (3, 70000), (70000, 3)]
+    jobs, host = _batch_jobs(ctx, lengths, 41)
+    jobs.append((jobs[5][0], jobs[5][1], jobs[5][0], jobs[5][1], jobs[-1][4].clone()))   # shared operand
+    host.append((host[5][0], host[5][0]))
+    for rep in range(3):                      # call 1 direct, call 2 captures, call 3 replays
+        for j in jobs:
+            j[4].fill_(-1)
+        ctx.mul_batch(jobs)
+        for (da, na, db, nb, c), (a, b) in zip(jobs, host):
+            nc = na + nb - 1 if na and nb else 0
+            if nc == 0:
+                continue
+            assert np.array_equal(host_words(c, nc), O.mul(a, na, b, nb)), (rep, na, nb)
+
+
+def host_words(t, nbits):
+    return host(t)[: (nbits + 63) // 64]
+
+
+def test_batch_config4_4096_products(ctx):
+    # 4096 products, operand lengths log-uniform in [2^10, 2^20] bits, a and b independent
+    lens = synth.loguniform_lengths(synth.config_seed(4, 0), 8192, 10.0, 20.0).reshape(4096, 2)
+    lengths = [(int(x), int(y)) for x, y in lens]
+    jobs, host = _batch_jobs(ctx, lengths, 44)
+    ctx.mul_batch(jobs)
+    lows = O.random_irreducibles(synth.config_seed(4, 99), 8)
+    rng2 = random.Random(4)
+    sample = set(rng2.sample(range(4096), 48))
+    for k, ((da, na, db, nb, c), (a, b)) in enumerate(zip(jobs, host)):
+        got = host_words(c, na + nb - 1)
+        if k in sample:
+            assert np.array_equal(got, O.mul(a, na, b, nb)), (k, na, nb)
+        else:
+            assert O.modcheck(a, na, b, nb, got, na + nb - 1, lows).all(), (k, na, nb)
