@@ -43,6 +43,10 @@ CONFIGS = {
     1: dict(na=1 << 16, nb=1 << 16, name="single product 2^16 x 2^16 bits, uniform random"),
     2: dict(na=1 << 24, nb=1 << 24, name="single product 2^24 x 2^24 bits, uniform random"),
     3: dict(na=1 << 30, nb=1 << 30, name="single product 2^30 x 2^30 bits, uniform random"),
+    4: dict(name="4096 independent products, operand lengths log-uniform in [2^10, 2^20] bits, a and b drawn "
+                 "independently, uniform random bits, one gf2x_mul_batch call per step"),
+    5: dict(name="serving: Poisson arrivals of products, operand lengths log-uniform in [2^12, 2^26] bits, "
+                 "5% with one operand of exactly 2^28 bits, continuous batching over 3 streams"),
 }
 METRIC = "operand Gbit/s (na+nb bits per product / time)"
 UNIT = "Gbit/s"
@@ -186,6 +190,8 @@ def scaled_oracle_workload(na, nb):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.config == 4:
+        return run_reference_batch(args)
     cfg = CONFIGS[args.config]
     na, nb = scaled_oracle_workload(cfg["na"], cfg["nb"])
     from oracle import clmul as O
@@ -212,6 +218,36 @@ def run_reference(args, world, rank):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args):
+    """The oracle on the batched mix: each step multiplies a bounded sample (256 of the products)."""
+    from oracle import clmul as O
+    O.build()
+    lens = synth.loguniform_lengths(synth.config_seed(4, 100), 2 * args.batch, 10.0, 20.0).reshape(args.batch, 2)
+    sample = 256
+    def one_step(offset):
+        t = 0.0
+        for k in range(sample):
+            na, nb = int(lens[(offset + k) % args.batch, 0]), int(lens[(offset + k) % args.batch, 1])
+            a = synth.operand(synth.config_seed(4, 10000 + 2 * k), na)
+            b = synth.operand(synth.config_seed(4, 10001 + 2 * k), nb)
+            t0 = time.perf_counter()
+            O.mul(a, na, b, nb)
+            t += time.perf_counter() - t0
+        return t
+    for w in range(args.warmup):
+        one_step(w * sample)
+    total = sum(one_step(s * sample) for s in range(args.steps))
+    value = sample * args.steps / total
+    line = {"impl": "reference", "metric": "products/s (batched, uneven lengths)", "value": value, "unit": "products/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": CONFIGS[4]["name"], "products": args.batch},
+            "cpu_baseline": {"value": value, "unit": "products/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{sample} products of the mix per step"},
+            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -409,6 +445,227 @@ def run_stage(args):
     ctx.close()
 
 
+def make_jobs(ctx, count, lo, hi, seed, dev):
+    import torch
+    lens = synth.loguniform_lengths(synth.config_seed(4, seed), 2 * count, lo, hi).reshape(count, 2)
+    jobs, hosts = [], []
+    for k in range(count):
+        na, nb = int(lens[k, 0]), int(lens[k, 1])
+        a = synth.operand(synth.config_seed(4, 10000 + 2 * k), na)
+        b = synth.operand(synth.config_seed(4, 10001 + 2 * k), nb)
+        c = torch.empty((na + nb - 1 + 63) // 64, dtype=torch.int64, device=dev)
+        jobs.append((torch.from_numpy(a.view(np.int64)).to(dev), na, torch.from_numpy(b.view(np.int64)).to(dev), nb, c))
+        hosts.append((a, b))
+    return jobs, hosts
+
+
+def run_batch(args, world, rank, local):
+    """Batched products/s (one gf2x_mul_batch per step) vs one gf2x_mul call per product."""
+    import torch
+    from paper_1803_11301_gb300 import Context, build as lib_build, workspace_bytes
+    lib_build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream(dev)
+    count = args.batch
+    jobs, hosts = make_jobs(ctx, count, 10.0, 20.0, 100 + rank, dev)
+    ws = torch.empty(ctx.batch_workspace_bytes(jobs), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx.profile_enable(True)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        ctx.mul_batch(jobs, workspace=ws, stream=stream)
+    torch.cuda.synchronize(dev)
+    ctx.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dist_barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.fill_(k)
+        starts[k].record(stream)
+        ctx.mul_batch(jobs, workspace=ws, stream=stream)
+        ends[k].record(stream)
+        ctx.profile_read()
+    torch.cuda.synchronize(dev)
+    dist_barrier(world)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    total_ms = dist_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world)
+    value = world * count * args.steps / (total_ms / 1e3)
+    # one gf2x_mul per product (sequential calls on the same stream), one pass after one warm-up pass
+    wsp = torch.empty(max(workspace_bytes(j[1], j[3]) for j in jobs), dtype=torch.uint8, device=dev)
+    for j in jobs:
+        ctx.mul(j[0], j[1], j[2], j[3], out=j[4], workspace=wsp, stream=stream)
+    torch.cuda.synchronize(dev)
+    flush.fill_(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in jobs:
+        ctx.mul(j[0], j[1], j[2], j[3], out=j[4], workspace=wsp, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = dist_max(e0.elapsed_time(e1), world)
+    plain = world * count / (plain_ms / 1e3)
+    # end to end: operands from pinned host memory, results back, inside the timed region
+    pins = [(torch.from_numpy(a.view(np.int64)).pin_memory(), torch.from_numpy(b.view(np.int64)).pin_memory())
+            for a, b in hosts]
+    outs = [torch.empty(j[4].numel(), dtype=torch.int64).pin_memory() for j in jobs]
+
+    def e2e_step():
+        for (pa, pb), j in zip(pins, jobs):
+            j[0].copy_(pa, non_blocking=True)
+            j[2].copy_(pb, non_blocking=True)
+        ctx.mul_batch(jobs, workspace=ws, stream=stream)
+        for o, j in zip(outs, jobs):
+            o.copy_(j[4], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = dist_max(time.perf_counter() - t0, world)
+    h2d = sum((j[1] + 63) // 64 * 8 + (j[3] + 63) // 64 * 8 for j in jobs)
+    d2h = sum(j[4].numel() * 8 for j in jobs)
+    launches = sum(v[1] for v in prof.values())
+    line = {"metric": "products/s (batched, uneven lengths)", "value": value, "unit": "products/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": CONFIGS[4]["name"], "products": count,
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "plain": {"value": plain, "unit": "products/s", "how": "one gf2x_mul call per product, same stream"},
+            "batched_over_plain": value / plain,
+            "operand_gbits": world * sum(j[1] + j[3] for j in jobs) * args.steps / (total_ms / 1e3) / 1e9,
+            "stages_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+            "gpu_launches": int(launches), "clocks": clk,
+            "e2e": {"value": world * count * args.steps / e2e_s, "unit": "products/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def serving_requests(count, seed):
+    """(na, nb) per request: log-uniform 2^12..2^26, 5% with one operand of exactly 2^28 bits."""
+    lens = synth.loguniform_lengths(synth.config_seed(5, seed), 2 * count, 12.0, 26.0).reshape(count, 2)
+    u = synth.uniform01(synth.config_seed(5, seed + 1), 2 * count).reshape(count, 2)
+    out = []
+    for k in range(count):
+        na, nb = int(lens[k, 0]), int(lens[k, 1])
+        if u[k, 0] < 0.05:
+            if u[k, 1] < 0.5:
+                na = 1 << 28
+            else:
+                nb = 1 << 28
+        out.append((na, nb))
+    return out
+
+
+def run_serving(args, world, rank, local):
+    """Continuous batching vs one gf2x_mul per request, same Poisson arrival stream."""
+    import torch
+    from paper_1803_11301_gb300 import Context, build as lib_build, workspace_bytes
+    from paper_1803_11301_gb300.serving import Server, Request, percentile
+    lib_build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = Context(local)
+    count = args.requests
+    sizes = serving_requests(count, 7 + rank)
+    # device-resident operand pools; a request uses a prefix of a pool entry
+    small = [torch.from_numpy(synth.operand(synth.config_seed(5, 100 + k), 1 << 26).view(np.int64)).to(dev)
+             for k in range(8)]
+    big = [torch.from_numpy(synth.operand(synth.config_seed(5, 200 + k), 1 << 28).view(np.int64)).to(dev)
+           for k in range(2)]
+
+    def operand(bits, k):
+        pool = big if bits > (1 << 26) else small
+        return pool[k % len(pool)]
+
+    def make(k):
+        na, nb = sizes[k]
+        return Request(operand(na, 3 * k), na, operand(nb, 3 * k + 1), nb, tag=k)
+
+    # saturated: everything queued at once
+    srv = Server(ctx, streams=3)
+    for k in range(min(count, 400)):                        # warm-up
+        srv.submit(make(k))
+    srv.drain()
+    torch.cuda.synchronize(dev)
+    srv = Server(ctx, streams=3)
+    t0 = time.perf_counter()
+    for k in range(count):
+        srv.submit(make(k))
+    srv.drain()
+    sat_s = time.perf_counter() - t0
+    sat = count / sat_s
+    # arrivals: Poisson at 0.8 x saturated
+    lam = args.load * sat
+    gaps = -np.log(1.0 - synth.uniform01(synth.config_seed(5, 55), count)) / lam
+    arrivals = np.cumsum(gaps)
+
+    def replay(submit_fn, poll_fn, done_fn):
+        start = time.perf_counter()
+        k = 0
+        while k < count or not done_fn():
+            now = time.perf_counter() - start
+            while k < count and arrivals[k] <= now:
+                submit_fn(k, start + arrivals[k])
+                k += 1
+            poll_fn()
+        return time.perf_counter() - start
+
+    srv = Server(ctx, streams=3)
+    reqs = []
+
+    def s_submit(k, t):
+        r = make(k)
+        r.arrival = t
+        reqs.append(r)
+        srv.submit(r)
+    wall = replay(s_submit, srv.poll, lambda: not srv.pending and not srv.inflight)
+    lat = [1e3 * (r.done - r.arrival) for r in reqs]
+    served = {"products_per_s": count / wall, "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+              "batches": srv._next_batch}
+    # one gf2x_mul per request, in arrival order on one stream
+    stream = torch.cuda.current_stream(dev)
+    wsp = torch.empty(max(workspace_bytes(na, nb) for na, nb in sizes), dtype=torch.uint8, device=dev)
+    plain_pending = []
+    plain_lat = []
+
+    def p_submit(k, t):
+        na, nb = sizes[k]
+        out = torch.empty((na + nb - 1 + 63) // 64, dtype=torch.int64, device=dev)
+        ctx.mul(operand(na, 3 * k), na, operand(nb, 3 * k + 1), nb, out=out, workspace=wsp, stream=stream)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        plain_pending.append((t, ev, out))
+
+    def p_poll():
+        now = time.perf_counter()
+        while plain_pending and plain_pending[0][1].query():
+            t, _, _ = plain_pending.pop(0)
+            plain_lat.append(1e3 * (now - t))
+    pwall = replay(p_submit, p_poll, lambda: not plain_pending)
+    plain = {"products_per_s": count / pwall, "p50_ms": percentile(plain_lat, 50), "p99_ms": percentile(plain_lat, 99)}
+    line = {"metric": "products/s under Poisson load (continuous batching)", "value": served["products_per_s"],
+            "unit": "products/s", "n_gpus": world, "steps": count, "warmup": min(count, 400),
+            "ms_per_step": 1e3 * wall / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": CONFIGS[5]["name"], "requests": count, "load": args.load,
+                       "arrival_rate_per_s": lam, "saturated_products_per_s": sat},
+            "served": served, "plain_one_call_per_request": plain,
+            "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,6 +673,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf2x", choices=["gf2x", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
+    ap.add_argument("--batch", type=int, default=4096, help="products per batch for --config 4")
+    ap.add_argument("--requests", type=int, default=2000, help="requests for --config 5")
+    ap.add_argument("--load", type=float, default=0.8, help="arrival rate / saturated rate for --config 5")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage", default=None,
@@ -434,7 +694,12 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_setup(args.gpus)
-    run_gpu(args, world, rank, local)
+    if args.config == 4:
+        run_batch(args, world, rank, local)
+    elif args.config == 5:
+        run_serving(args, world, rank, local)
+    else:
+        run_gpu(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -293,3 +293,26 @@ def test_batch_config4_4096_products(ctx):
             assert np.array_equal(got, O.mul(a, na, b, nb)), (k, na, nb)
         else:
             assert O.modcheck(a, na, b, nb, got, na + nb - 1, lows).all(), (k, na, nb)
+
+
+def test_serving_results_same_alone_and_in_the_mix(ctx):
+    # overlapping batches on several streams; every result equals the product computed alone
+    import torch
+    from paper_1803_11301_gb300.serving import Server, Request
+    lens = synth.loguniform_lengths(synth.config_seed(5, 3), 300, 8.0, 18.0).reshape(150, 2)
+    pool = [dev(synth.operand(synth.config_seed(5, 300 + k), 1 << 18)) for k in range(4)]
+    srv = Server(ctx, streams=3, max_batch=16)
+    reqs = []
+    for k in range(150):
+        r = Request(pool[k % 4], int(lens[k, 0]), pool[(k + 1) % 4], int(lens[k, 1]), tag=k)
+        reqs.append(r)
+        srv.submit(r)
+        if k % 7 == 0:
+            srv.poll()                                   # arrivals interleave with running batches
+    srv.drain()
+    torch.cuda.synchronize()
+    assert srv._next_batch > 3
+    for r in reqs:
+        alone = ctx.mul(r.a, r.na, r.b, r.nb)
+        nc = r.na + r.nb - 1
+        assert torch.equal(r.out[: (nc + 63) // 64], alone), r.tag
