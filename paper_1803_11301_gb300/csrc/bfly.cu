@@ -31,7 +31,7 @@ namespace gf2x {
 namespace {
 
 constexpr int kBottom = 11;          // bottom tile: 2^11 points (16 KiB per transform)
-constexpr int kTableMin = 6;         // bottom layers >= 6 multiply through tables
+constexpr int kTableMin = 4;         // bottom layers >= 4 multiply through tables
 constexpr int kChunkTabs = 16;       // bottom tables built at a time (32 KiB)
 constexpr int kTopLayers = 4;        // layers per top pass
 constexpr int kThreads = 256;

@@ -315,6 +315,19 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, 
     std::vector<Step> steps;
     build_steps(K, 1, steps);
     if (steps.empty()) return cudaSuccess;
+    // For K >= 16 the list ends with the 32 steps of BasisCvt inside every
+    // 2^16-bit block; those run in the register kernel of cvt16.cu (first
+    // for the inverse, last for the forward transform).
+    const bool unit16 = K >= 16;
+    if (unit16) {
+        steps.resize(steps.size() - 32);
+        if (inverse) {
+            cudaError_t e = basis_cvt_unit16(ctx, bits, L, true, count, stride, st);
+            if (e != cudaSuccess || steps.empty()) return e;
+        } else if (steps.empty()) {
+            return basis_cvt_unit16(ctx, bits, L, false, count, stride, st);
+        }
+    }
     if (inverse) std::vector<Step>(steps.rbegin(), steps.rend()).swap(steps);
     if (!g_configured) {
         cudaFuncSetAttribute(k_cvt_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
@@ -389,6 +402,11 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, 
                                                                                                          stride);
         }
         count_launch(ctx);
+    }
+    if (unit16 && !inverse) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return basis_cvt_unit16(ctx, bits, L, false, count, stride, st);
     }
     return cudaGetLastError();
 }

@@ -125,6 +125,8 @@ namespace gf2x {
 // Batched forms: `count` jobs whose buffers are `stride` words apart
 // (count = 1, stride = 0 for a single product).
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
+// BasisCvt inside every 2^16-bit block of an L-bit array (L a multiple of 2^16).
+cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
 cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
                    cudaStream_t st);
