@@ -313,7 +313,8 @@ gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStr
         if (r.jobs) TRY(gf2x::load_jobs(ctx, r.jobs, which, r.T, r.stride, r.n / 64, r.count, st));
         else TRY(gf2x::load_bits(ctx, which ? r.b : r.a, which ? r.nb : r.na, r.T, r.n / 64, st));
     }
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, st)); }
+    // F (the Encode output, free until then) is the scratch buffer of BasisCvt
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st)); }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, st)); }
     return GF2X_OK;
 }
@@ -335,7 +336,8 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
     { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, Y ? Y : X, l, cnt, sd, st)); }
     { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, cnt, sd, st)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, r.T, cnt, sd, st)); }
-    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, st)); }
+    // X is free once Decode has read it: the scratch buffer of iBasisCvt
+    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st)); }
     {
         StageScope g(ctx, STAGE_STORE, st);
         if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
@@ -764,7 +766,7 @@ gf2x_status gf2x_basis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stre
     if (!valid_n(L)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_BASISCVT, (cudaStream_t)stream);
-    return from_cuda(gf2x::basis_cvt(ctx, bits, L, false, 1, 0, (cudaStream_t)stream));
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, false, 1, 0, nullptr, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *stream)
@@ -774,7 +776,7 @@ gf2x_status gf2x_ibasis_cvt(gf2x_ctx *ctx, uint64_t *bits, uint64_t L, void *str
     if (!valid_n(L)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_IBASISCVT, (cudaStream_t)stream);
-    return from_cuda(gf2x::basis_cvt(ctx, bits, L, true, 1, 0, (cudaStream_t)stream));
+    return from_cuda(gf2x::basis_cvt(ctx, bits, L, true, 1, 0, nullptr, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64_t *f, void *stream)

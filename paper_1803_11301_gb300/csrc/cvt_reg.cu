@@ -1,0 +1,340 @@
+// Register-resident parts of BasisCvt / iBasisCvt (Alg. 1, Sec. 2.3.1).
+//
+// (1) The conversion of every aligned 2^16-bit block on its own.  For a
+// length 2^K with 16 <= K <= 32, Alg. 1 splits at tau = 2^16 (the largest 2^i
+// with i a power of two and i <= K - 1), so its last part is the same
+// algorithm inside every block of 2^16 bits; for K >= 33 it splits at 2^32
+// and the 2^32-bit blocks again end with it.  Its step list, the flattening
+// described in cvt.cu, is fixed: 32 (h, d) steps, generated below at compile
+// time.  One warp per block: lane L holds the 32 consecutive words 32L ..
+// 32L+31 (2048 bits).  A step whose segments fit in 2048 bits runs inside
+// every lane with fixed register indices; a wider step (h >= 2^11, 15 of the
+// 32) pairs lane L of the lower half of a segment with lane L + h/2048 of the
+// upper half and moves the words it needs with warp shuffles.  No barrier is
+// taken between steps; shared memory only turns the coalesced load (lane L
+// gets words L, L+32, ...) into the per-lane layout and back, with an XOR
+// swizzle that keeps both sides free of bank conflicts.
+//
+// (2) The "outer" conversion of Alg. 1 on whole units: BasisCvt of length
+// 2^M whose coefficients are units of U words (the outer step of a split at
+// tau = U bits).  Every step then moves whole units, lo[q] ^= hi'[q - D], so
+// each of the U word columns is an independent BasisCvt of 2^M words.  A lane
+// group of min(2^M, 32) lanes holds one column, 2^M / 32 units per lane, and
+// runs the compile-time step list of BasisCvt(2^M) with the same
+// register/shuffle scheme as (1), here without bit shifts.
+#include "gf2x_common.cuh"
+
+namespace gf2x {
+namespace {
+
+constexpr int kUnitWords = 1024;        // 2^16 bits
+
+struct StepList {
+    int n;
+    signed char lh[40], ld[40];         // log2 h, log2 d (bits)
+};
+
+// Same recursion as the host planner: Taylor steps at s_i = x^tau + x, then
+// the outer conversion (unit tau), then the inner one (unit 1).
+constexpr void gen_steps(StepList &s, int K, int ulog)
+{
+    if (K <= 1) return;
+    int i = 1;
+    while (2 * i <= K - 1) i *= 2;
+    for (int k = K - i - 1; k >= 0; --k) {
+        s.lh[s.n] = (signed char)(i + k + ulog);
+        s.ld[s.n] = (signed char)(k + ulog);
+        ++s.n;
+    }
+    gen_steps(s, K - i, ulog + i);
+    gen_steps(s, i, ulog);
+}
+
+constexpr StepList make_steps(int K)
+{
+    StepList s{};
+    gen_steps(s, K, 0);
+    return s;
+}
+
+constexpr StepList kSteps16 = make_steps(16);
+static_assert(kSteps16.n == 32, "BasisCvt of 2^16 bits has 32 steps");
+
+template <int M>
+struct StepsOf {
+    static constexpr StepList list = make_steps(M);
+};
+
+constexpr u64 seg_mask(int h, int lo_bit, int hi_bit)
+{
+    // bits [lo_bit, hi_bit) of every 2h-bit segment of a word (h < 64)
+    u64 one = ((1ull << (hi_bit - lo_bit)) - 1) << lo_bit;
+    u64 m = 0;
+    for (int s = 0; s < 64; s += 2 * h) m |= one << s;
+    return m;
+}
+
+__device__ __forceinline__ u64 shfl(u64 v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// One step of a conversion whose elements are whole words (h = H = 2^LH and
+// d = D = 2^LD elements), on a column held by a group of lanes with R
+// consecutive elements per lane; gl is the lane's index in its group.
+// Forward: hi' = hi with its quotient fix hi[r] ^= hi[H - D + r] (r < D),
+// then lo[q] ^= hi'[q - D].  Inverse: the lo update with the current hi, then
+// the fix.
+template <int R, int LH, int LD, bool INV>
+__device__ __forceinline__ void wstep(u64 (&w)[R], int gl, int lane)
+{
+    constexpr int H = 1 << LH, D = 1 << LD;
+    if constexpr (2 * H <= R) {
+        // segments inside one lane
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * H) {
+            if (!INV) {
+#pragma unroll
+                for (int r = 0; r < D; ++r) w[b + H + r] ^= w[b + 2 * H - D + r];
+            }
+#pragma unroll
+            for (int q = D; q < H; ++q) w[b + q] ^= w[b + H + q - D];
+            if (INV) {
+#pragma unroll
+                for (int r = 0; r < D; ++r) w[b + H + r] ^= w[b + 2 * H - D + r];
+            }
+        }
+    } else {
+        // segments of 2P lanes: lane s < P of a segment holds lo elements,
+        // lane s >= P the hi elements at the same offsets
+        constexpr int P = H / R;
+        const int s = gl & (2 * P - 1);
+        const int base = lane - s;
+        const u64 lo_mask = s < P ? ~0ull : 0ull;
+        if constexpr (D < R) {
+            // hi[r] ^= hi[H - D + r] for r < D: first hi lane, from the last one
+            auto fix = [&]() {
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    const u64 t = shfl(w[R - D + r], base + 2 * P - 1);
+                    if (s == P) w[r] ^= t;
+                }
+            };
+            if (!INV) fix();
+            // element j of lo lane s takes element j - D of hi lane s (or
+            // element R + j - D of hi lane s - 1)
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                u64 v;
+                if (j >= D) {
+                    v = shfl(w[j - D], lane + P);
+                } else {
+                    v = shfl(w[R + j - D], lane + P - 1);
+                    if (s == 0) v = 0;
+                }
+                w[j] ^= v & lo_mask;
+            }
+            if (INV) fix();
+        } else {
+            // whole lanes: DL = D/R.  Lo lane s >= DL takes hi lane s - DL
+            // (lane + P - DL); hi lane s < P + DL is fixed from lane + P - DL.
+            constexpr int DL = D / R;
+            const u64 fix_mask = (s >= P && s < P + DL) ? ~0ull : 0ull;
+            const u64 lo_take = (s >= DL && s < P) ? ~0ull : 0ull;
+            if (!INV) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & fix_mask;
+#pragma unroll
+                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & lo_take;
+            } else {
+                // sources of both updates are unfixed hi lanes
+#pragma unroll
+                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & (fix_mask | lo_take);
+            }
+        }
+    }
+}
+
+// One step (h = 2^LH, d = 2^LD bits) on the 2^16-bit block held by the warp.
+// Forward: hi' = hi with its quotient fix, lo ^= (hi' << d) mod x^h.
+// Inverse: lo ^= (hi << d) mod x^h with the current hi, then the fix.
+// Steps with d >= 64 bits move whole words: wstep with 32 words per lane.
+template <int LH, int LD, bool INV>
+__device__ __forceinline__ void step(u64 (&w)[32], int lane)
+{
+    if constexpr (LD >= 6) {
+        wstep<32, LH - 6, LD - 6, INV>(w, lane, lane);
+    } else if constexpr (LH < 6) {
+        // segments inside one word
+        constexpr int h = 1 << LH, d = 1 << LD, sh = h - d;
+        constexpr u64 ma = seg_mask(h, h, h + d);      // bottom d bits of hi
+        constexpr u64 mb = seg_mask(h, d, h);          // lo bits [d, h)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            u64 x = w[j];
+            if (!INV) {
+                x ^= (x >> sh) & ma;
+                x ^= (x >> sh) & mb;
+            } else {
+                x ^= (x >> sh) & mb;
+                x ^= (x >> sh) & ma;
+            }
+            w[j] = x;
+        }
+    } else if constexpr (LH <= 10) {
+        // segments of 2hw <= 32 words inside one lane; d < 64 bits
+        constexpr int hw = 1 << (LH - 6), d = 1 << LD;
+#pragma unroll
+        for (int b = 0; b < 32; b += 2 * hw) {
+            if (!INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
+#pragma unroll
+            for (int q = hw - 1; q >= 0; --q) {
+                u64 t = w[b + hw + q] << d;
+                if (q > 0) t |= w[b + hw + q - 1] >> (64 - d);
+                w[b + q] ^= t;
+            }
+            if (INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
+        }
+    } else {
+        // segments of 2P lanes (lane s < P of a segment holds lo words, lane
+        // s >= P the hi words at the same offsets); d < 64 bits
+        constexpr int P = 1 << (LH - 11), d = 1 << LD;
+        const int s = lane & (2 * P - 1);
+        const int base = lane - s;
+        const u64 lo_mask = s < P ? ~0ull : 0ull;
+        // the fix: hi[0] ^= hi[hw-1] >> (64 - d), on the first hi lane
+        auto fix = [&]() {
+            const u64 top = shfl(w[31], base + 2 * P - 1);
+            if (s == P) w[0] ^= top >> (64 - d);
+        };
+        if (!INV) fix();
+        // lo[q] ^= (hi[q] << d) | (hi[q-1] >> (64 - d))
+        u64 prev = shfl(w[31], lane + P - 1);
+        if (s == 0) prev = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const u64 v = shfl(w[j], lane + P);
+            w[j] ^= ((v << d) | (prev >> (64 - d))) & lo_mask;
+            prev = v;
+        }
+        if (INV) fix();
+    }
+}
+
+template <bool INV, int I>
+__device__ __forceinline__ void run_steps(u64 (&w)[32], int lane)
+{
+    if constexpr (I < 32) {
+        // forward order, or the reversed list for the inverse
+        constexpr int k = INV ? 31 - I : I;
+        step<kSteps16.lh[k], kSteps16.ld[k], INV>(w, lane);
+        run_steps<INV, I + 1>(w, lane);
+    }
+}
+
+// One warp per 2^16-bit block; blockIdx.y is the job of a batch.
+template <bool INV>
+__global__ void __launch_bounds__(32) k_cvt_unit16(u64 *bits, u64 stride)
+{
+    __shared__ u64 stage[kUnitWords];
+    const int lane = threadIdx.x;
+    u64 *g = bits + (u64)blockIdx.y * stride + (u64)blockIdx.x * kUnitWords;
+    // word 32i + j is kept at 32i + (j ^ i)
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) stage[32 * i + (lane ^ i)] = g[32 * i + lane];
+    __syncwarp();
+    u64 w[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) w[j] = stage[32 * lane + (j ^ lane)];
+    run_steps<INV, 0>(w, lane);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stage[32 * lane + (j ^ lane)] = w[j];
+    __syncwarp();
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) g[32 * i + lane] = stage[32 * i + (lane ^ i)];
+}
+
+template <int M, bool INV, int I>
+__device__ __forceinline__ void run_outer_steps(u64 (&w)[(1 << M) >= 32 ? (1 << M) / 32 : 1], int gl, int lane)
+{
+    constexpr StepList S = StepsOf<M>::list;
+    if constexpr (I < S.n) {
+        constexpr int k = INV ? S.n - 1 - I : I;
+        wstep<((1 << M) >= 32 ? (1 << M) / 32 : 1), S.lh[k], S.ld[k], INV>(w, gl, lane);
+        run_outer_steps<M, INV, I + 1>(w, gl, lane);
+    }
+}
+
+constexpr int kOuterThreads = 256;      // 8 warps: 8 (or more) adjacent columns per block
+
+// Outer BasisCvt(2^M) on units of 2^ulog words: unit r, column c of chunk ch
+// is word (ch 2^M + r) 2^ulog + c.  Lane group (chunk, column) holds the
+// column; consecutive warps take consecutive columns.
+template <int M, bool INV>
+__global__ void __launch_bounds__(kOuterThreads) k_cvt_outer(u64 *bits, const u64 *src, int ulog, u64 stride)
+{
+    constexpr int NU = 1 << M;
+    constexpr int LPC = NU < 32 ? NU : 32;              // lanes per column
+    constexpr int R = NU / LPC;                         // units per lane
+    constexpr int CPW = 32 / LPC;                       // columns per warp
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LPC - 1);
+    const u64 col = ((u64)blockIdx.x * (kOuterThreads / 32) + (threadIdx.x >> 5)) * CPW + (u64)(lane / LPC);
+    const u64 ch = col >> ulog, c = col & ((1ull << ulog) - 1);
+    const u64 off = (u64)blockIdx.y * stride + ((ch << M) << ulog) + c;
+    u64 *g = bits + off;
+    const u64 *gs = src + off;
+    u64 w[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) w[j] = gs[(u64)(gl * R + j) << ulog];
+    run_outer_steps<M, INV, 0>(w, gl, lane);
+#pragma unroll
+    for (int j = 0; j < R; ++j) g[(u64)(gl * R + j) << ulog] = w[j];
+}
+
+template <int M>
+void launch_outer(u64 *bits, const u64 *src, int ulog, u64 columns, bool inverse, int count, u64 stride,
+                  cudaStream_t st)
+{
+    constexpr int LPC = (1 << M) < 32 ? (1 << M) : 32;
+    const u64 threads = columns * LPC;
+    const dim3 grid((unsigned)(threads / kOuterThreads), (unsigned)count);
+    if (inverse) k_cvt_outer<M, true><<<grid, kOuterThreads, 0, st>>>(bits, src, ulog, stride);
+    else k_cvt_outer<M, false><<<grid, kOuterThreads, 0, st>>>(bits, src, ulog, stride);
+}
+
+}  // namespace
+
+cudaError_t basis_cvt_outer(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L, int M, int ulog, bool inverse, int count,
+                            u64 stride, cudaStream_t st)
+{
+    if (M <= 1) return src == bits ? cudaSuccess : cudaErrorInvalidValue;   // no steps (length <= 2)
+    const u64 words = L >> 6;
+    const u64 columns = words >> M;                     // (chunks) x (words per unit)
+    const u64 lpc = (1ull << M) < 32 ? (1ull << M) : 32;
+    if (M > 9 || ulog < 0 || (columns * lpc) % kOuterThreads != 0 || (columns >> ulog) << ulog != columns)
+        return cudaErrorInvalidValue;
+    switch (M) {
+    case 2: launch_outer<2>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 3: launch_outer<3>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 4: launch_outer<4>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 5: launch_outer<5>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 6: launch_outer<6>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 7: launch_outer<7>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    case 8: launch_outer<8>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    default: launch_outer<9>(bits, src, ulog, columns, inverse, count, stride, st); break;
+    }
+    count_launch(ctx);
+    return cudaGetLastError();
+}
+
+cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st)
+{
+    const u64 units = L >> 16;
+    if (units == 0) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)units, (unsigned)count);
+    if (inverse) k_cvt_unit16<true><<<grid, 32, 0, st>>>(bits, stride);
+    else k_cvt_unit16<false><<<grid, 32, 0, st>>>(bits, stride);
+    count_launch(ctx);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2x

@@ -124,9 +124,18 @@ namespace gf2x {
 
 // Batched forms: `count` jobs whose buffers are `stride` words apart
 // (count = 1, stride = 0 for a single product).
-cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
+// BasisCvt (or iBasisCvt) in place on bits.  `scratch`, if not null, is a
+// buffer laid out like `bits` (count x stride words) whose contents may be
+// overwritten; with it, 2^18 <= L <= 2^32 run the structured kernels.
+cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
+                      cudaStream_t st);
 // BasisCvt inside every 2^16-bit block of an L-bit array (L a multiple of 2^16).
 cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
+// Outer BasisCvt of length 2^M (2 <= M <= 9) on units of 2^ulog words, applied
+// to every chunk of 2^M units of an L-bit array, read from src (which may be
+// bits) and written to bits.
+cudaError_t basis_cvt_outer(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L, int M, int ulog, bool inverse, int count,
+                            u64 stride, cudaStream_t st);
 cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
                    cudaStream_t st);
