@@ -10,7 +10,7 @@
  * word w is the coefficient of x^(64 w + t).
  *
  *   oracle_clmul64   one 64x64 -> 128-bit carry-less product (4-bit windows)
- *   oracle_mul       schoolbook below 16 words, Karatsuba above, OpenMP tasks
+ *   oracle_mul       schoolbook up to 32 words, Karatsuba above, OpenMP tasks
  *                    on the top levels, longer operand cut into chunks
  *   oracle_modcheck  c mod p == (a mod p)(b mod p) mod p for seeded random
  *                    irreducible monic p of degree 64 (Rabin's test)
