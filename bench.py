@@ -66,9 +66,14 @@ NUM_SMS = 152
 PRODUCTS_PER_SM_CLOCK = 1.0
 BOTTOM_LAYERS = 11            # low layers done by the fused bottom kernel
 
-# ncu dram bytes per launch of the dominant kernel, from profiles/ (None when
-# the kernel changed since the capture).
-TRAFFIC_BYTES_PER_LAUNCH = None
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a stage's
+# kernel, keyed by (stage, na, nb), from one capture of the same workload
+# (profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md).
+# An entry is removed when its kernel changes; a missing entry reports null.
+TRAFFIC_BYTES_PER_LAUNCH = {
+    ("bottom_fused", 1 << 24, 1 << 24): 8430592 + 0,
+    ("bottom_fused", 1 << 30, 1 << 30): 537287168 + 225268224,
+}
 
 
 def load_peaks():
@@ -394,12 +399,12 @@ def run_gpu(args, world, rank, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s", "frac": achieved / peak,
                 "peak_source": (f"derived: {NUM_SMS} SMs x {sm_max_mhz:.0f} MHz x {PRODUCTS_PER_SM_CLOCK:g} GF(2^64) "
                                 "product per SM-clock (shared-memory port bound of the table product)"),
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH, "kernel_stage": dom,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb)), "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
     else:
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH, "kernel_stage": dom,
+                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb)), "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
 
     compulsory = ((na + 63) // 64 + (nb + 63) // 64 + (nc + 63) // 64) * 8

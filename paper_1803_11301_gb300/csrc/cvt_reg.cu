@@ -263,42 +263,93 @@ __device__ __forceinline__ void run_outer_steps(u64 (&w)[(1 << M) >= 32 ? (1 << 
     }
 }
 
-constexpr int kOuterThreads = 256;      // 8 warps: 8 (or more) adjacent columns per block
+// Block shape of the outer kernel: 16 warps (8 for M = 9, whose 16 units per
+// lane take more registers), one column per warp for M >= 5.
+template <int M>
+struct OuterShape {
+    static constexpr int NU = 1 << M;                   // units per column
+    static constexpr int LPC = NU < 32 ? NU : 32;       // lanes per column
+    static constexpr int R = NU / LPC;                  // units per lane
+    static constexpr int CPW = 32 / LPC;                // columns per warp
+    static constexpr int WARPS = M >= 9 ? 8 : 16;
+    static constexpr int THREADS = WARPS * 32;
+    static constexpr int CW = WARPS * CPW;              // columns per block
+    static constexpr int S = NU + 1;                    // shared-memory column stride (odd)
+    // lanes of a column hold units gl R .. gl R + R - 1; unit j of lane gl sits
+    // at gl R + (j ^ sigma(gl)), so the 32 lanes reading their j-th unit hit
+    // 16 different bank pairs (two lanes each)
+    static __device__ __forceinline__ int slot(int gl, int j)
+    {
+        constexpr int spread = R >= 16 ? 1 : 16 / R;
+        return gl * R + (j ^ ((gl / spread) & (R - 1)));
+    }
+};
 
 // Outer BasisCvt(2^M) on units of 2^ulog words: unit r, column c of chunk ch
-// is word (ch 2^M + r) 2^ulog + c.  Lane group (chunk, column) holds the
-// column; consecutive warps take consecutive columns.
+// is word (ch 2^M + r) 2^ulog + c.  A block takes CW adjacent columns: their
+// unit rows are staged through shared memory (coalesced 8-byte cp.async, one
+// row segment of CW words per unit), each lane group takes one column into
+// registers, runs the steps, and the rows go back the same way.
 template <int M, bool INV>
-__global__ void __launch_bounds__(kOuterThreads) k_cvt_outer(u64 *bits, const u64 *src, int ulog, u64 stride)
+__global__ void __launch_bounds__(OuterShape<M>::THREADS) k_cvt_outer(u64 *bits, const u64 *src, int ulog, u64 stride)
 {
-    constexpr int NU = 1 << M;
-    constexpr int LPC = NU < 32 ? NU : 32;              // lanes per column
-    constexpr int R = NU / LPC;                         // units per lane
-    constexpr int CPW = 32 / LPC;                       // columns per warp
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (LPC - 1);
-    const u64 col = ((u64)blockIdx.x * (kOuterThreads / 32) + (threadIdx.x >> 5)) * CPW + (u64)(lane / LPC);
-    const u64 ch = col >> ulog, c = col & ((1ull << ulog) - 1);
-    const u64 off = (u64)blockIdx.y * stride + ((ch << M) << ulog) + c;
+    using Sh = OuterShape<M>;
+    constexpr int NU = Sh::NU, LPC = Sh::LPC, R = Sh::R, CW = Sh::CW, S = Sh::S;
+    __shared__ u64 st[CW * S];
+    const u64 col0 = (u64)blockIdx.x * CW;
+    const u64 ch = col0 >> ulog, c0 = col0 & ((1ull << ulog) - 1);
+    const u64 off = (u64)blockIdx.y * stride + ((ch << M) << ulog) + c0;
     u64 *g = bits + off;
     const u64 *gs = src + off;
+    // rows in: element (unit r, column w) -> st[w S + slot(r / R, r % R)]
+    for (int e = threadIdx.x; e < NU * CW; e += Sh::THREADS) {
+        const int r = e / CW, w = e % CW;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(st + w * S + Sh::slot(r / R, r % R));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gs + ((u64)r << ulog) + w)
+                     : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LPC - 1);
+    const int w0 = (threadIdx.x >> 5) * Sh::CPW + lane / LPC;   // this lane group's column
     u64 w[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) w[j] = gs[(u64)(gl * R + j) << ulog];
+    for (int j = 0; j < R; ++j) w[j] = st[w0 * S + Sh::slot(gl, j)];
     run_outer_steps<M, INV, 0>(w, gl, lane);
 #pragma unroll
-    for (int j = 0; j < R; ++j) g[(u64)(gl * R + j) << ulog] = w[j];
+    for (int j = 0; j < R; ++j) st[w0 * S + Sh::slot(gl, j)] = w[j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NU * CW; e += Sh::THREADS) {
+        const int r = e / CW, w = e % CW;
+        g[((u64)r << ulog) + w] = st[w * S + Sh::slot(r / R, r % R)];
+    }
 }
 
 template <int M>
 void launch_outer(u64 *bits, const u64 *src, int ulog, u64 columns, bool inverse, int count, u64 stride,
                   cudaStream_t st)
 {
-    constexpr int LPC = (1 << M) < 32 ? (1 << M) : 32;
-    const u64 threads = columns * LPC;
-    const dim3 grid((unsigned)(threads / kOuterThreads), (unsigned)count);
-    if (inverse) k_cvt_outer<M, true><<<grid, kOuterThreads, 0, st>>>(bits, src, ulog, stride);
-    else k_cvt_outer<M, false><<<grid, kOuterThreads, 0, st>>>(bits, src, ulog, stride);
+    using Sh = OuterShape<M>;
+    const dim3 grid((unsigned)(columns / Sh::CW), (unsigned)count);
+    if (inverse) k_cvt_outer<M, true><<<grid, Sh::THREADS, 0, st>>>(bits, src, ulog, stride);
+    else k_cvt_outer<M, false><<<grid, Sh::THREADS, 0, st>>>(bits, src, ulog, stride);
+}
+
+// Columns per block of the outer kernel for M (0 if M is out of range).
+int outer_columns_per_block(int M)
+{
+    switch (M) {
+    case 2: return OuterShape<2>::CW;
+    case 3: return OuterShape<3>::CW;
+    case 4: return OuterShape<4>::CW;
+    case 5: return OuterShape<5>::CW;
+    case 6: return OuterShape<6>::CW;
+    case 7: return OuterShape<7>::CW;
+    case 8: return OuterShape<8>::CW;
+    case 9: return OuterShape<9>::CW;
+    default: return 0;
+    }
 }
 
 }  // namespace
@@ -309,8 +360,9 @@ cudaError_t basis_cvt_outer(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L, int
     if (M <= 1) return src == bits ? cudaSuccess : cudaErrorInvalidValue;   // no steps (length <= 2)
     const u64 words = L >> 6;
     const u64 columns = words >> M;                     // (chunks) x (words per unit)
-    const u64 lpc = (1ull << M) < 32 ? (1ull << M) : 32;
-    if (M > 9 || ulog < 0 || (columns * lpc) % kOuterThreads != 0 || (columns >> ulog) << ulog != columns)
+    const int cw = outer_columns_per_block(M);
+    // every block's columns lie in one chunk: CW divides the unit
+    if (cw == 0 || ulog < 0 || (1ull << ulog) % (u64)cw != 0 || (columns >> ulog) << ulog != columns)
         return cudaErrorInvalidValue;
     switch (M) {
     case 2: launch_outer<2>(bits, src, ulog, columns, inverse, count, stride, st); break;
