@@ -70,10 +70,7 @@ BOTTOM_LAYERS = 11            # low layers done by the fused bottom kernel
 # kernel, keyed by (stage, na, nb), from one capture of the same workload
 # (profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md).
 # An entry is removed when its kernel changes; a missing entry reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {
-    ("bottom_fused", 1 << 24, 1 << 24): 8430592 + 0,
-    ("bottom_fused", 1 << 30, 1 << 30): 537287168 + 225268224,
-}
+TRAFFIC_BYTES_PER_LAUNCH = {}
 
 
 def load_peaks():

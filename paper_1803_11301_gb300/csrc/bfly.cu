@@ -46,14 +46,36 @@ __device__ __forceinline__ u64 mul_xpow(u64 c, int e)
 
 // Window w keeps entry e at slot e ^ w, so that the 16 threads writing one
 // window each (build) and the 32 lanes reading one window (lookup) touch
-// distinct bank pairs.
-__device__ __forceinline__ u64 mul_tab(const u64 *__restrict__ tab, u64 x)
+// distinct bank pairs.  `tab` is the table's shared-memory address, 128-byte
+// aligned: XORing nibble w of x with w is one XOR of x with 0xFEDCBA98..10,
+// and the byte offset (slot * 8) of window w is one shift and one LOP3 that
+// also ORs in the table address; the window's 128-byte base is the load's
+// immediate offset.
+template <int W>
+__device__ __forceinline__ void tab_window(u64 &r, unsigned tab, unsigned lo, unsigned hi)
+{
+    constexpr int k = 4 * (W & 7);                      // bit of nibble W in its half
+    const unsigned src = W < 8 ? lo : hi;
+    const unsigned a = ((k >= 3 ? src >> (k - 3) : src << (3 - k)) & 0x78u) | tab;
+    u64 v;
+    asm volatile("ld.shared.u64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(W * 128));
+    r ^= v;
+    if constexpr (W < 15) tab_window<W + 1>(r, tab, lo, hi);
+}
+
+__device__ __forceinline__ u64 mul_tab(unsigned tab, u64 x)
 {
     u64 r = 0;
-#pragma unroll
-    for (int w = 0; w < 16; ++w) r ^= tab[w * 16 + ((((unsigned)(x >> (4 * w))) & 15u) ^ (unsigned)w)];
+    tab_window<0>(r, tab, (unsigned)x ^ 0x76543210u, (unsigned)(x >> 32) ^ 0xFEDCBA98u);
     return r;
 }
+
+// Shared-memory address of p.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Dynamic shared memory rounded up to 128 bytes (launches request 128 more):
+// the table addresses must be 128-byte aligned for mul_tab.
+__device__ __forceinline__ u64 *align128(u64 *p) { return (u64 *)(((uintptr_t)p + 127) & ~(uintptr_t)127); }
 
 __device__ __forceinline__ u64 mul_x(u64 p) { return (p << 1) ^ ((p >> 63) * GF2X_MOD_LOW); }
 
@@ -102,7 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
                                                        const u64 *__restrict__ cvt, const u64 *__restrict__ vb,
                                                        int arrays, u64 stride)
 {
-    extern __shared__ u64 tabs[];
+    extern __shared__ u64 smem_raw[];
+    u64 *tabs = align128(smem_raw);
     constexpr int ntab = (1 << M) - 1;
     // blockIdx.y = job * arrays + array; jobs of a batch are `stride` words apart
     const u64 job = blockIdx.y / arrays;
@@ -129,11 +152,11 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
         for (int s2 = 0; s2 < M; ++s2) {
             const int r = INV ? s2 : M - 1 - s2;
             const int half = 1 << r;
-            const u64 *tl = tabs + (size_t)((1 << (M - 1 - r)) - 1) * kTab;
+            const unsigned tl = smem_addr(tabs) + (unsigned)(((1 << (M - 1 - r)) - 1) * kTab * 8);
 #pragma unroll
             for (int u = 0; u < (1 << M); ++u) {
                 if (u & half) continue;
-                const u64 *tb = tl + (size_t)(u >> (r + 1)) * kTab;
+                const unsigned tb = tl + (unsigned)((u >> (r + 1)) * kTab * 8);
                 if (!INV) {
                     v[u] ^= mul_tab(tb, v[u | half]);
                     v[u | half] ^= v[u];
@@ -189,7 +212,7 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
         for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
             const int blk = j0 + (t >> i), jj = t & (span - 1);
             const int s0 = (blk << (i + 1)) + jj;
-            const u64 *tb = tabs + (size_t)(blk - j0) * kTab;
+            const unsigned tb = smem_addr(tabs) + (unsigned)((blk - j0) * kTab * 8);
             u64 x0 = a[s0], x1 = a[s0 + span];
             if (!inverse) {
                 x0 ^= mul_tab(tb, x1);
@@ -215,7 +238,8 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
 __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
                                                           const u64 *__restrict__ vb, int mode, u64 stride)
 {
-    extern __shared__ u64 sm[];
+    extern __shared__ u64 smem_raw[];
+    u64 *sm = align128(smem_raw);
     X += (u64)blockIdx.y * stride;                      // job of a batch
     if (Y) Y += (u64)blockIdx.y * stride;
     const int T = 1 << bt;
@@ -261,14 +285,14 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
 
 size_t bottom_smem(int bt, bool fused)
 {
-    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)kChunkTabs * kTab) * sizeof(u64);
+    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)kChunkTabs * kTab) * sizeof(u64) + 128;
 }
 
 template <int M, bool INV>
 void launch_top(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
                 const u64 *cvt, const u64 *vb, int arrays, u64 stride)
 {
-    size_t smem = (size_t)((1 << M) - 1) * kTab * sizeof(u64);
+    size_t smem = (size_t)((1 << M) - 1) * kTab * sizeof(u64) + 128;
     k_bfly_top<M, INV><<<grid, kThreads, smem, st>>>(x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride);
 }
 
