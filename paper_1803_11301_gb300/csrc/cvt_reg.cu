@@ -152,22 +152,86 @@ __device__ __forceinline__ void wstep(u64 (&w)[R], int gl, int lane)
     }
 }
 
-// One step (h = 2^LH, d = 2^LD bits) on the 2^16-bit block held by the warp.
+// Word index p of a 2^16-bit block -> its slot in shared memory: word 32a + b
+// at 32a + (b ^ a).  Lanes that hold R consecutive words each (R = 8, 16 or
+// 32) and read or write their j-th word together hit 16 bank pairs, two lanes
+// each; so do 32 lanes that take 32 consecutive words.
+__device__ __forceinline__ int unit_slot(int p) { return (p & ~31) | ((p & 31) ^ ((p >> 5) & 31)); }
+
+// A step whose segments span several warps, through shared memory: every
+// thread stores its words, then takes what it needs from that snapshot
+// (forward: lo[q] ^= hi'[q - dw], hi' = hi with the quotient fix; inverse: the
+// lo update with the snapshot hi; both: the fix of hi[r] for r < dw).
+template <int R, int LH, int LD, bool INV>
+__device__ __forceinline__ void xstep(u64 (&w)[R], int t, u64 *sm)
+{
+    constexpr int hw = 1 << (LH - 6);
+    __syncthreads();                                    // the previous readers of sm are done
+#pragma unroll
+    for (int j = 0; j < R; ++j) sm[unit_slot(t * R + j)] = w[j];
+    __syncthreads();
+    const int p0 = t * R;
+    const int q0 = p0 & (2 * hw - 1);                   // offset in the segment; all R words in one half
+    const int sb = p0 - q0;
+    auto at = [&](int x) { return sm[unit_slot(sb + x)]; };
+    if (q0 < hw) {
+        if constexpr (LD >= 6) {
+            constexpr int dw = 1 << (LD - 6);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int q = q0 + j;
+                if (q < dw) continue;
+                const int x = q - dw;
+                u64 v = at(hw + x);
+                if (!INV && x < dw) v ^= at(2 * hw - dw + x);
+                w[j] ^= v;
+            }
+        } else {
+            constexpr int d = 1 << LD;
+            const u64 fix0 = INV ? 0 : at(2 * hw - 1) >> (64 - d);   // hi'[0] = hi[0] ^ fix0
+            u64 prev = q0 > 0 ? at(hw + q0 - 1) : 0;
+            if (q0 == 1) prev ^= fix0;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                u64 v = at(hw + q0 + j);
+                if (q0 + j == 0) v ^= fix0;
+                w[j] ^= (v << d) | (prev >> (64 - d));
+                prev = v;
+            }
+        }
+    } else {
+        const int r0 = q0 - hw;
+        if constexpr (LD >= 6) {
+            constexpr int dw = 1 << (LD - 6);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (r0 + j < dw) w[j] ^= at(2 * hw - dw + r0 + j);
+        } else {
+            constexpr int d = 1 << LD;
+            if (r0 == 0) w[0] ^= at(2 * hw - 1) >> (64 - d);
+        }
+    }
+}
+
+// One step (h = 2^LH, d = 2^LD bits) on a 2^16-bit block held by 1024/R
+// threads, R consecutive words each (thread t: words tR .. tR + R - 1).
 // Forward: hi' = hi with its quotient fix, lo ^= (hi' << d) mod x^h.
 // Inverse: lo ^= (hi << d) mod x^h with the current hi, then the fix.
-// Steps with d >= 64 bits move whole words: wstep with 32 words per lane.
-template <int LH, int LD, bool INV>
-__device__ __forceinline__ void step(u64 (&w)[32], int lane)
+// Steps with d >= 64 bits move whole words (wstep); wider than a warp: xstep.
+template <int R, int LH, int LD, bool INV>
+__device__ __forceinline__ void step(u64 (&w)[R], int t, int lane, u64 *sm)
 {
-    if constexpr (LD >= 6) {
-        wstep<32, LH - 6, LD - 6, INV>(w, lane, lane);
+    if constexpr (LH >= 6 && (2 << (LH - 6)) > 32 * R) {
+        xstep<R, LH, LD, INV>(w, t, sm);
+    } else if constexpr (LD >= 6) {
+        wstep<R, LH - 6, LD - 6, INV>(w, lane, lane);
     } else if constexpr (LH < 6) {
         // segments inside one word
         constexpr int h = 1 << LH, d = 1 << LD, sh = h - d;
         constexpr u64 ma = seg_mask(h, h, h + d);      // bottom d bits of hi
         constexpr u64 mb = seg_mask(h, d, h);          // lo bits [d, h)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < R; ++j) {
             u64 x = w[j];
             if (!INV) {
                 x ^= (x >> sh) & ma;
@@ -178,38 +242,38 @@ __device__ __forceinline__ void step(u64 (&w)[32], int lane)
             }
             w[j] = x;
         }
-    } else if constexpr (LH <= 10) {
-        // segments of 2hw <= 32 words inside one lane; d < 64 bits
+    } else if constexpr ((2 << (LH - 6)) <= R) {
+        // segments of 2hw <= R words inside one lane; d < 64 bits
         constexpr int hw = 1 << (LH - 6), d = 1 << LD;
 #pragma unroll
-        for (int b = 0; b < 32; b += 2 * hw) {
+        for (int b = 0; b < R; b += 2 * hw) {
             if (!INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
 #pragma unroll
             for (int q = hw - 1; q >= 0; --q) {
-                u64 t = w[b + hw + q] << d;
-                if (q > 0) t |= w[b + hw + q - 1] >> (64 - d);
-                w[b + q] ^= t;
+                u64 t2 = w[b + hw + q] << d;
+                if (q > 0) t2 |= w[b + hw + q - 1] >> (64 - d);
+                w[b + q] ^= t2;
             }
             if (INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
         }
     } else {
         // segments of 2P lanes (lane s < P of a segment holds lo words, lane
         // s >= P the hi words at the same offsets); d < 64 bits
-        constexpr int P = 1 << (LH - 11), d = 1 << LD;
+        constexpr int P = (1 << (LH - 6)) / R, d = 1 << LD;
         const int s = lane & (2 * P - 1);
         const int base = lane - s;
         const u64 lo_mask = s < P ? ~0ull : 0ull;
         // the fix: hi[0] ^= hi[hw-1] >> (64 - d), on the first hi lane
         auto fix = [&]() {
-            const u64 top = shfl(w[31], base + 2 * P - 1);
+            const u64 top = shfl(w[R - 1], base + 2 * P - 1);
             if (s == P) w[0] ^= top >> (64 - d);
         };
         if (!INV) fix();
         // lo[q] ^= (hi[q] << d) | (hi[q-1] >> (64 - d))
-        u64 prev = shfl(w[31], lane + P - 1);
+        u64 prev = shfl(w[R - 1], lane + P - 1);
         if (s == 0) prev = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < R; ++j) {
             const u64 v = shfl(w[j], lane + P);
             w[j] ^= ((v << d) | (prev >> (64 - d))) & lo_mask;
             prev = v;
@@ -218,38 +282,40 @@ __device__ __forceinline__ void step(u64 (&w)[32], int lane)
     }
 }
 
-template <bool INV, int I>
-__device__ __forceinline__ void run_steps(u64 (&w)[32], int lane)
+template <int R, bool INV, int I>
+__device__ __forceinline__ void run_steps(u64 (&w)[R], int t, int lane, u64 *sm)
 {
     if constexpr (I < 32) {
         // forward order, or the reversed list for the inverse
         constexpr int k = INV ? 31 - I : I;
-        step<kSteps16.lh[k], kSteps16.ld[k], INV>(w, lane);
-        run_steps<INV, I + 1>(w, lane);
+        step<R, kSteps16.lh[k], kSteps16.ld[k], INV>(w, t, lane, sm);
+        run_steps<R, INV, I + 1>(w, t, lane, sm);
     }
 }
 
-// One warp per 2^16-bit block; blockIdx.y is the job of a batch.
-template <bool INV>
-__global__ void __launch_bounds__(32) k_cvt_unit16(u64 *bits, u64 stride)
+// One block of 1024/R threads per 2^16-bit block; blockIdx.y is the job of a
+// batch.  Words go through shared memory in both directions so that global
+// accesses are coalesced (thread t takes words t, t + 1024/R, ...).
+template <bool INV, int R>
+__global__ void __launch_bounds__(1024 / R) k_cvt_unit16(u64 *bits, u64 stride)
 {
-    __shared__ u64 stage[kUnitWords];
-    const int lane = threadIdx.x;
+    constexpr int NT = 1024 / R;
+    __shared__ u64 sm[kUnitWords];
+    const int t = threadIdx.x, lane = t & 31;
     u64 *g = bits + (u64)blockIdx.y * stride + (u64)blockIdx.x * kUnitWords;
-    // word 32i + j is kept at 32i + (j ^ i)
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) stage[32 * i + (lane ^ i)] = g[32 * i + lane];
-    __syncwarp();
-    u64 w[32];
+    for (int i = 0; i < R; ++i) sm[unit_slot(NT * i + t)] = g[NT * i + t];
+    __syncthreads();
+    u64 w[R];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) w[j] = stage[32 * lane + (j ^ lane)];
-    run_steps<INV, 0>(w, lane);
-    __syncwarp();
+    for (int j = 0; j < R; ++j) w[j] = sm[unit_slot(t * R + j)];
+    run_steps<R, INV, 0>(w, t, lane, sm);
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) stage[32 * lane + (j ^ lane)] = w[j];
-    __syncwarp();
+    for (int j = 0; j < R; ++j) sm[unit_slot(t * R + j)] = w[j];
+    __syncthreads();
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) g[32 * i + lane] = stage[32 * i + (lane ^ i)];
+    for (int i = 0; i < R; ++i) g[NT * i + t] = sm[unit_slot(NT * i + t)];
 }
 
 template <int M, bool INV, int I>
@@ -378,15 +444,35 @@ cudaError_t basis_cvt_outer(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L, int
     return cudaGetLastError();
 }
 
-cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st)
+// With R words per thread: R = 32 (one warp per block) keeps every step in
+// registers and shuffles; R = 8 (four warps) runs the 7 steps wider than a
+// warp through shared memory but has four times the threads in flight, which
+// pays when there are few blocks.
+cudaError_t basis_cvt_unit16_r(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, int R,
+                               cudaStream_t st)
 {
     const u64 units = L >> 16;
     if (units == 0) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)units, (unsigned)count);
-    if (inverse) k_cvt_unit16<true><<<grid, 32, 0, st>>>(bits, stride);
-    else k_cvt_unit16<false><<<grid, 32, 0, st>>>(bits, stride);
+    switch (R * 2 + (inverse ? 1 : 0)) {
+    case 16: k_cvt_unit16<false, 8><<<grid, 128, 0, st>>>(bits, stride); break;
+    case 17: k_cvt_unit16<true, 8><<<grid, 128, 0, st>>>(bits, stride); break;
+    case 32: k_cvt_unit16<false, 16><<<grid, 64, 0, st>>>(bits, stride); break;
+    case 33: k_cvt_unit16<true, 16><<<grid, 64, 0, st>>>(bits, stride); break;
+    case 64: k_cvt_unit16<false, 32><<<grid, 32, 0, st>>>(bits, stride); break;
+    case 65: k_cvt_unit16<true, 32><<<grid, 32, 0, st>>>(bits, stride); break;
+    default: return cudaErrorInvalidValue;
+    }
     count_launch(ctx);
     return cudaGetLastError();
+}
+
+cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st)
+{
+    // measured on GB300: R = 8 up to 512 blocks (2^25 bits), R = 32 from 1024
+    const u64 blocks = (L >> 16) * (u64)count;
+    const int R = blocks <= 4 * (u64)ctx->num_sms ? 8 : 32;
+    return basis_cvt_unit16_r(ctx, bits, L, inverse, count, stride, R, st);
 }
 
 }  // namespace gf2x
