@@ -315,18 +315,44 @@ gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStr
     }
     // F (the Encode output, free until then) is the scratch buffer of BasisCvt
     { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st)); }
-    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, st)); }
+    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, r.stride, st)); }
+    return GF2X_OK;
+}
+
+// Lines 1-2 and 4-5 of Alg. 5 for both operands of one product in the same
+// launches, when they convert at the same length L <= n/2: a in the lower half
+// of T and b in the upper half (two jobs n/128 words apart); BasisCvt's scratch
+// is X with the same layout; Encode writes a's points to X and b's to Y.
+gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
+{
+    const int l = log2_u64(r.n) - 6;
+    const u64 half = r.n / 128;
+    {
+        StageScope s(ctx, STAGE_LOAD, st);
+        TRY(gf2x::load_pair(ctx, r.a, r.na, r.b, r.nb, r.T, half, half, st));
+    }
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.La, false, 2, half, r.X, st)); }
+    {
+        StageScope s(ctx, STAGE_ENCODE, st);
+        TRY(gf2x::encode(ctx, r.T, l, r.X, r.La, 2, half, (u64)(r.Y - r.X), st));
+    }
     return GF2X_OK;
 }
 
 gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 {
     const int l = log2_u64(r.n) - 6;
-    gf2x_status s = forward(ctx, r, 0, r.X, st);
-    if (s != GF2X_OK) return s;
-    if (!r.square) {
-        s = forward(ctx, r, 1, r.Y, st);
+    gf2x_status s;
+    if (!r.jobs && !r.square && r.count == 1 && r.La == r.Lb && 2 * r.La <= r.n) {
+        s = forward_pair(ctx, r, st);
         if (s != GF2X_OK) return s;
+    } else {
+        s = forward(ctx, r, 0, r.X, st);
+        if (s != GF2X_OK) return s;
+        if (!r.square) {
+            s = forward(ctx, r, 1, r.Y, st);
+            if (s != GF2X_OK) return s;
+        }
     }
     u64 *X = r.X, *Y = r.square ? nullptr : r.Y;
     const int cnt = r.count;
@@ -786,7 +812,7 @@ gf2x_status gf2x_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64
     if (!valid_n(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
-    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, n, 1, 0, (cudaStream_t)stream));
+    return from_cuda(gf2x::encode(ctx, novel, log2_u64(n) - 6, f, n, 1, 0, 0, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)

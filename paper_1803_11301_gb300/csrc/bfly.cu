@@ -15,7 +15,7 @@
 //
 // Bottom tile (layers < kBottom): 2^kBottom consecutive points in shared
 // memory, one layer after the other.  Layers i >= kTableMin (twiddle shared by
-// 2^i butterflies per array) use tables, built kChunkTabs at a time; layers
+// 2^i butterflies per array) use tables, built 32 at a time; layers
 // 0..kTableMin-1 multiply with the integer form.  In the fused mode the tile holds the matching tiles of both
 // transforms: forward A, forward B, pointwise product, inverse (Alg. 5 lines
 // 3, 6, 7, 8 for the low layers) in one pass over HBM.
@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kBottom = 11;          // bottom tile: 2^11 points (16 KiB per transform)
 constexpr int kTableMin = 4;         // bottom layers >= 4 multiply through tables
-constexpr int kChunkTabs = 16;       // bottom tables built at a time (32 KiB)
 constexpr int kTopLayers = 4;        // layers per top pass
 constexpr int kThreads = 256;
 constexpr int kTab = 256;            // u64 entries per multiplication table
@@ -198,16 +197,17 @@ __device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, cons
 }
 
 // Layer i >= kTableMin on the tile(s): the 2^(bt-1-i) twiddles of the layer
-// c_j = v_{l+32-i} + Cantor((base >> i) + 2j) get tables kChunkTabs at a time;
+// c_j = v_{l+32-i} + Cantor((base >> i) + 2j) get tables CHUNK at a time;
 // each chunk's butterflies run on every array of the pass (A and B together).
+template <int CHUNK>
 __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, const u64 *__restrict__ cvt,
                             const u64 *__restrict__ vb, u64 *tabs, bool inverse)
 {
     const int ntot = 1 << (bt - 1 - i);
     const int span = 1 << i;
     const u64 vtop = vb[l + 32 - i];
-    for (int j0 = 0; j0 < ntot; j0 += kChunkTabs) {
-        const int nt = ntot - j0 < kChunkTabs ? ntot - j0 : kChunkTabs;
+    for (int j0 = 0; j0 < ntot; j0 += CHUNK) {
+        const int nt = ntot - j0 < CHUNK ? ntot - j0 : CHUNK;
         build_tables(tabs, nt, [&](int t) { return vtop ^ cantor(cvt, (base >> i) + ((u64)(j0 + t) << 1)); });
         for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
             const int blk = j0 + (t >> i), jj = t & (span - 1);
@@ -235,7 +235,8 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
+template <int THREADS, int CHUNK>
+__global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
                                                           const u64 *__restrict__ vb, int mode, u64 stride)
 {
     extern __shared__ u64 smem_raw[];
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
     if (mode != BOTTOM_INV) {
         for (int i = bt - 1; i >= 0; --i) {
             if (i >= kTableMin) {
-                table_layer(a, b, bt, i, l, base, cvt, vb, tabs, false);
+                table_layer<CHUNK>(a, b, bt, i, l, base, cvt, vb, tabs, false);
             } else {
                 const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
                 tile_layer(a, bt, i, ctop, cvt, false);
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
     if (mode != BOTTOM_FWD) {
         for (int i = 0; i < bt; ++i) {
             if (i >= kTableMin) {
-                table_layer(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
+                table_layer<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
             } else {
                 const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
                 tile_layer(a, bt, i, ctop, cvt, true);
@@ -283,9 +284,31 @@ __global__ void __launch_bounds__(kThreads) k_bfly_bottom(u64 *X, u64 *Y, int l,
     for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
 }
 
-size_t bottom_smem(int bt, bool fused)
+size_t bottom_smem(int bt, bool fused, int chunk)
 {
-    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)kChunkTabs * kTab) * sizeof(u64) + 128;
+    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)chunk * kTab) * sizeof(u64) + 128;
+}
+
+// Bottom kernel shapes (threads per block, tables built at a time): with few
+// tiles, 512 threads and 32-table chunks keep more warps in flight (2 blocks
+// per SM); with many tiles, 256 threads and 16-table chunks fit 3 blocks per
+// SM and issue better (measured on GB300: 91.7 vs 95.8 us at 256 tiles,
+// 4.48 vs 4.08 ms at 16384 tiles).
+constexpr int kBottomThreadsSmall = 512, kBottomChunkSmall = 32;
+constexpr int kBottomThreadsLarge = 256, kBottomChunkLarge = 16;
+
+void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride, cudaStream_t st)
+{
+    const u64 tiles = 1ull << (l - bt);
+    const bool fused = mode == BOTTOM_FUSED;
+    const dim3 grid((unsigned)tiles, count);
+    if (tiles * (u64)count < 4 * (u64)ctx->num_sms)
+        k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall><<<grid, kBottomThreadsSmall,
+            bottom_smem(bt, fused, kBottomChunkSmall), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+    else
+        k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge><<<grid, kBottomThreadsLarge,
+            bottom_smem(bt, fused, kBottomChunkLarge), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+    count_launch(ctx);
 }
 
 template <int M, bool INV>
@@ -335,7 +358,10 @@ bool configured = false;
 void configure()
 {
     if (configured) return;
-    cudaFuncSetAttribute(k_bfly_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkSmall));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLarge));
     configured = true;
 }
 
@@ -352,9 +378,7 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
         if (e != cudaSuccess) return e;
     }
     if (bt > 0) {
-        k_bfly_bottom<<<dim3((unsigned)(1ull << (l - bt)), count), kThreads, bottom_smem(bt, false), st>>>(
-            x, nullptr, l, bt, ctx->d_cvt, ctx->d_cantor, inverse ? BOTTOM_INV : BOTTOM_FWD, stride);
-        count_launch(ctx);
+        launch_bottom(ctx, x, nullptr, l, bt, inverse ? BOTTOM_INV : BOTTOM_FWD, count, stride, st);
     }
     if (inverse) return top_passes(ctx, x, nullptr, l, bt, true, count, stride, st);
     return cudaGetLastError();
@@ -374,9 +398,7 @@ cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int cou
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    k_bfly_bottom<<<dim3((unsigned)(1ull << (l - bt)), count), kThreads, bottom_smem(bt, true), st>>>(
-        X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, BOTTOM_FUSED, stride);
-    count_launch(ctx);
+    launch_bottom(ctx, X, Y, l, bt, BOTTOM_FUSED, count, stride, st);
     return cudaGetLastError();
 }
 

@@ -54,10 +54,11 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
 constexpr int kPad = kCols + 1;      // padded row of the staging tile
 
 __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, int rows,
-                                                const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups, u64 stride)
+                                                const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups, u64 stride,
+                                                u64 out_stride)
 {
     novel += (u64)blockIdx.y * stride;            // job of a batch
-    f += (u64)blockIdx.y * stride;
+    f += (u64)blockIdx.y * out_stride;
     __shared__ u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
@@ -82,17 +83,18 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
 }
 
 // n_p < 64: the whole transform is at most 32 words; one block, bit by bit.
-__global__ void k_encode_small(const u64 *__restrict__ novel, int l, const u64 *__restrict__ enc, u64 *__restrict__ f,
-                               u64 stride)
+// Bits at or above nonzero_bits are zero and are not read.
+__global__ void k_encode_small(const u64 *__restrict__ novel, int l, u64 nonzero_bits, const u64 *__restrict__ enc,
+                               u64 *__restrict__ f, u64 stride, u64 out_stride)
 {
     novel += (u64)blockIdx.y * stride;
-    f += (u64)blockIdx.y * stride;
+    f += (u64)blockIdx.y * out_stride;
     const u64 np = 1ull << l;
     for (u64 i = threadIdx.x; i < np; i += blockDim.x) {
         u64 u = 0;
         for (int j = 0; j < 64; ++j) {
             u64 pos = (u64)j * np + i;
-            u |= ((novel[pos >> 6] >> (pos & 63)) & 1ull) << j;
+            if (pos < nonzero_bits) u |= ((novel[pos >> 6] >> (pos & 63)) & 1ull) << j;
         }
         f[i] = lin64(enc, u);
     }
@@ -172,6 +174,25 @@ __global__ void k_load_bits(const u64 *__restrict__ src, u64 nbits, u64 *__restr
     dst[w] = v;
 }
 
+// Both operands of one product: blockIdx.y = 0 loads a into dst, 1 loads b
+// into dst + half (dst_words words each, zero beyond the operand).
+__global__ void k_load_pair(const u64 *__restrict__ a, u64 na, const u64 *__restrict__ b, u64 nb, u64 *__restrict__ dst,
+                            u64 dst_words, u64 half)
+{
+    const u64 *src = blockIdx.y ? b : a;
+    const u64 nbits = blockIdx.y ? nb : na;
+    dst += blockIdx.y * half;
+    const u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= dst_words) return;
+    const u64 nw = (nbits + 63) >> 6;
+    u64 v = 0;
+    if (w < nw) {
+        v = src[w];
+        if (w == nw - 1 && (nbits & 63)) v &= (~0ull) >> (64 - (nbits & 63));
+    }
+    dst[w] = v;
+}
+
 // Batch forms: job j of the launch (blockIdx.y) reads operand `which` of
 // jobs[j] into dst + j * stride, or writes its product from src + j * stride.
 __global__ void k_load_jobs(const JobDev *__restrict__ jobs, int which, u64 *__restrict__ dst, u64 stride,
@@ -210,17 +231,18 @@ inline unsigned blocks_for(u64 n, unsigned threads) { return (unsigned)((n + thr
 }  // namespace
 
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
-                   cudaStream_t st)
+                   u64 out_stride, cudaStream_t st)
 {
     if (l < 6) {
-        k_encode_small<<<dim3(1, count), 64, 0, st>>>(novel, l, ctx->d_enc, f, stride);
+        k_encode_small<<<dim3(1, count), 64, 0, st>>>(novel, l, nonzero_bits, ctx->d_enc, f, stride, out_stride);
     } else {
         const u64 rw = 1ull << (l - 6), np = 1ull << l;
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
         if (rows > 64) rows = 64;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
-        k_encode<<<dim3((unsigned)grid, count), 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups, stride);
+        k_encode<<<dim3((unsigned)grid, count), 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups, stride,
+                                                               out_stride);
     }
     count_launch(ctx);
     return cudaGetLastError();
@@ -253,6 +275,16 @@ cudaError_t load_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, u64 ds
 {
     if (dst_words) {
         k_load_bits<<<blocks_for(dst_words, 256), 256, 0, st>>>(src, nbits, dst, dst_words);
+        count_launch(ctx);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t load_pair(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *dst, u64 dst_words, u64 half,
+                      cudaStream_t st)
+{
+    if (dst_words) {
+        k_load_pair<<<dim3(blocks_for(dst_words, 256), 2), 256, 0, st>>>(a, na, b, nb, dst, dst_words, half);
         count_launch(ctx);
     }
     return cudaGetLastError();
