@@ -368,21 +368,25 @@ __global__ void __launch_bounds__(kThreads) k_cvt_col(u64 *bits, const u64 *src,
 // columns c, every dependency of a step goes from a column to columns on its
 // left, cyclically: lo[p] reads hi'[p - dw] (or hi'[p], hi'[p-1] for d < 64
 // bits), and the quotient fix brings the top dw words of the hi half to its
-// bottom; within one step the fix and the lo update together reach 2 max(dw,
-// 1) columns to the left.  So a block of threads holds, for every row of the
-// group, a window of W output columns plus `halo` columns to their left
-// (wrapping around to the top of the row), runs all mw layers on it in shared
-// memory, and writes back the W output columns, which are then exact.  The
+// bottom.  A block of threads holds, for every row of the group, a window of W
+// output columns plus `halo` columns to their left (wrapping around to the top
+// of the row), runs all mw layers on it in shared memory, and writes back the
+// W output columns, which are then exact (taylor_halo).  The
 // halo columns of one block are output columns of its neighbour, so the
 // kernel runs out of place (src != bits): no block reads what another writes.
 constexpr int kUnitWordsLog = 10;               // 2^16 bits
 constexpr int kTaylorThreads = 512;
 
+// Columns of halo for mw layers: the layers together shift by less than 2^mw
+// bits (the Taylor expansion at x^tau + x of a 2^mw-block group, written as
+// sums of x^(q-r) f_q, reaches q - r < 2^mw bits to the left, cyclically), so
+// ceil(2^mw / 64) + 1 words, rounded up to even (the kernel works on column
+// pairs).  Checked exact, against the step list, for every window position,
+// window widths 8, 16 and 32, and the depths in use (mw <= 8).
 __host__ __device__ constexpr int taylor_halo(int mw)
 {
-    int h = 0;
-    for (int k = 0; k < mw; ++k) h += 2 * ((k >= 6) ? (1 << (k - 6)) : 1);
-    return h;
+    const int h = ((1 << mw) + 63) / 64 + 1;
+    return (h + 1) & ~1;
 }
 
 __global__ void __launch_bounds__(kTaylorThreads) k_cvt_taylor(u64 *bits, const u64 *src, int mw, int W, int inverse,
