@@ -68,9 +68,12 @@ BOTTOM_LAYERS = 11            # low layers done by the fused bottom kernel
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a stage's
 # kernel, keyed by (stage, na, nb), from one capture of the same workload
-# (profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md).
+# (profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md gives both captures).
 # An entry is removed when its kernel changes; a missing entry reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_BYTES_PER_LAUNCH = {
+    ("bottom_fused", 1 << 24, 1 << 24): 8426240 + 0,
+    ("bottom_fused", 1 << 30, 1 << 30): 536919552 + 224388864,
+}
 
 
 def load_peaks():
