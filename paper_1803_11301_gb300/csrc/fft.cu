@@ -7,10 +7,18 @@ namespace {
 
 constexpr int kCols = 32;            // word columns per Encode/Decode block
 
-__device__ __forceinline__ void load_table(u64 *dst, const u64 *__restrict__ src)
+// Copy a 16 KiB window table (16-byte aligned: it sits in the context's
+// cudaMalloc'd table block) to shared memory with asynchronous 16-byte copies;
+// the caller waits (cp.async.wait_all) and synchronises.
+__device__ __forceinline__ void load_table_async(u64 *dst, const u64 *__restrict__ src)
 {
-    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) dst[k] = src[k];
+    for (int k = 2 * threadIdx.x; k < 8 * 256; k += 2 * blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst + k)),
+                     "l"(src + k)
+                     : "memory");
 }
+
+__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------- Encode
 // n_p = 2^l >= 64.  Row j of the novelpoly bit array is bits [j n_p, (j+1) n_p),
@@ -59,11 +67,11 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
 {
     novel += (u64)blockIdx.y * stride;            // job of a batch
     f += (u64)blockIdx.y * out_stride;
-    __shared__ u64 tab[8 * 256];
+    __shared__ __align__(16) u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    load_table(tab, enc);
+    load_table_async(tab, enc);                   // in flight with the first tile's loads
     for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
         const u64 w0 = g * cols;
         __syncthreads();
@@ -71,6 +79,7 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
             const int j = k / cols, w = k % cols;
             tile[j * kPad + w] = j < rows ? novel[(u64)j * rw + w0 + w] : 0;
         }
+        copy_async_wait();
         __syncthreads();
         for (int w = warp; w < cols; w += blockDim.x >> 5) {
             u64 A = tile[lane * kPad + w], B = tile[(lane + 32) * kPad + w];
@@ -108,11 +117,12 @@ __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 r
 {
     h += (u64)blockIdx.y * stride;
     novel += (u64)blockIdx.y * stride;
-    __shared__ u64 tab[8 * 256];
+    __shared__ __align__(16) u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    load_table(tab, dec);
+    load_table_async(tab, dec);
+    copy_async_wait();
     __syncthreads();
     for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
         const u64 w0 = g * cols;
