@@ -259,14 +259,14 @@ def run_reference_batch(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def stage_work(stage, na, nb, n, products, square=False):
+def stage_work(stage, na, nb, n, products):
     """Algorithmic work of one stage over `products` products: (amount, kind).
 
     kind "mul": GF(2^64) products (one per butterfly); kind "hbm": bytes."""
     l = n.bit_length() - 1 - 6
     n_p = 1 << l
     bt = min(BOTTOM_LAYERS, l)
-    fw = 1 if square else 2
+    fw = 2                         # two forward transforms
     la = max(64, 1 << max(0, (na - 1).bit_length()))
     lb = max(64, 1 << max(0, (nb - 1).bit_length()))
     if stage == "butterfly":       # top layers of the forward transforms
@@ -278,7 +278,7 @@ def stage_work(stage, na, nb, n, products, square=False):
     if stage == "pointwise":
         return products * n_p, "mul"
     if stage == "basis_cvt":       # read + write each operand's L bits once
-        return products * 2 * (la + (0 if square else lb)) // 8, "hbm"
+        return products * 2 * (la + lb) // 8, "hbm"
     if stage == "ibasis_cvt":
         return products * 2 * n // 8, "hbm"
     if stage == "encode":          # read n bits, write n_p words, per operand
@@ -286,7 +286,7 @@ def stage_work(stage, na, nb, n, products, square=False):
     if stage == "decode":
         return products * 2 * n // 8, "hbm"
     if stage == "load":
-        return products * ((na + 7) // 8 + n // 8 + (0 if square else (nb + 7) // 8 + n // 8)), "hbm"
+        return products * ((na + 7) // 8 + (nb + 7) // 8 + n // 8), "hbm"
     if stage == "store":
         nc = na + nb - 1
         return products * 2 * ((nc + 63) // 64) * 8, "hbm"

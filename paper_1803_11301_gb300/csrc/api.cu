@@ -300,7 +300,6 @@ struct ClassRun {
     u64 max_c_words;                // longest product of the class, in words
     u64 *X, *Y, *T;
     u64 stride;                     // words between the buffers of consecutive jobs
-    bool square;                    // a == b (direct form only): one forward transform
 };
 
 // Lines 1-2 (or 4-5) of Alg. 5 for one operand of every job: load, BasisCvt, Encode.
@@ -343,23 +342,21 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 {
     const int l = log2_u64(r.n) - 6;
     gf2x_status s;
-    if (!r.jobs && !r.square && r.count == 1 && r.La == r.Lb && 2 * r.La <= r.n) {
+    if (!r.jobs && r.count == 1 && r.La == r.Lb && 2 * r.La <= r.n) {
         s = forward_pair(ctx, r, st);
         if (s != GF2X_OK) return s;
     } else {
         s = forward(ctx, r, 0, r.X, st);
         if (s != GF2X_OK) return s;
-        if (!r.square) {
-            s = forward(ctx, r, 1, r.Y, st);
-            if (s != GF2X_OK) return s;
-        }
+        s = forward(ctx, r, 1, r.Y, st);
+        if (s != GF2X_OK) return s;
     }
-    u64 *X = r.X, *Y = r.square ? nullptr : r.Y;
+    u64 *X = r.X, *Y = r.Y;
     const int cnt = r.count;
     const u64 sd = r.stride;
     // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
     { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, X, Y, l, cnt, sd, st)); }
-    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, Y ? Y : X, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, Y, l, cnt, sd, st)); }
     { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, cnt, sd, st)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, r.T, cnt, sd, st)); }
     // X is free once Decode has read it: the scratch buffer of iBasisCvt
@@ -375,6 +372,12 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
                        cudaStream_t st)
 {
+    if (a == b && na == nb) {
+        // a * a: the Frobenius map spreads the bits of a; no transform
+        StageScope s(ctx, STAGE_STORE, st);
+        TRY(gf2x::square_bits(ctx, a, na, c, st));
+        return GF2X_OK;
+    }
     ClassRun r{};
     r.n = transform_bits(na, nb);
     r.count = 1;
@@ -386,7 +389,6 @@ gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb
     r.Y = (u64 *)((char *)ws + buf);
     r.T = (u64 *)((char *)ws + 2 * buf);
     r.stride = 0;
-    r.square = (a == b && na == nb);
     return run_class(ctx, r, st);
 }
 

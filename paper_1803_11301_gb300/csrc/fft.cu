@@ -184,6 +184,26 @@ __global__ void k_load_bits(const u64 *__restrict__ src, u64 nbits, u64 *__restr
     dst[w] = v;
 }
 
+// c = a * a.  In characteristic 2 squaring is the Frobenius map, additive:
+// (sum a_i x^i)^2 = sum a_i x^(2i), so bit i of a goes to bit 2i of c and no
+// transform is needed.  Output word w is the 32 bits [32w, 32w + 32) of a,
+// spread to the even positions.
+__global__ void k_square_bits(const u64 *__restrict__ a, u64 na, u64 *__restrict__ c, u64 nc_words)
+{
+    const u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nc_words) return;
+    const u64 src = w >> 1, nw = (na + 63) >> 6;
+    u64 v = a[src];
+    if (src == nw - 1 && (na & 63)) v &= (~0ull) >> (64 - (na & 63));
+    u64 x = (w & 1) ? v >> 32 : v & 0xFFFFFFFFull;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    c[w] = x;
+}
+
 // Both operands of one product: blockIdx.y = 0 loads a into dst, 1 loads b
 // into dst + half (dst_words words each, zero beyond the operand).
 __global__ void k_load_pair(const u64 *__restrict__ a, u64 na, const u64 *__restrict__ b, u64 nb, u64 *__restrict__ dst,
@@ -295,6 +315,16 @@ cudaError_t load_pair(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
 {
     if (dst_words) {
         k_load_pair<<<dim3(blocks_for(dst_words, 256), 2), 256, 0, st>>>(a, na, b, nb, dst, dst_words, half);
+        count_launch(ctx);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t square_bits(gf2x_ctx *ctx, const u64 *a, u64 na, u64 *c, cudaStream_t st)
+{
+    const u64 nc_words = (2 * na - 1 + 63) >> 6;
+    if (na) {
+        k_square_bits<<<blocks_for(nc_words, 256), 256, 0, st>>>(a, na, c, nc_words);
         count_launch(ctx);
     }
     return cudaGetLastError();
