@@ -49,6 +49,8 @@ CONFIGS = {
                  "independently, uniform random bits, one gf2x_mul_batch call per step"),
     5: dict(name="serving: Poisson arrivals of products, operand lengths log-uniform in [2^12, 2^26] bits, "
                  "5% with one operand of exactly 2^28 bits, continuous batching over 3 streams"),
+    6: dict(na=1 << 24, nb=1 << 24, name="reused operand: 2^24 x 2^24-bit products a_k * b with one fixed b, "
+                                        "b's transform computed once (gf2x_forward_transform) outside the timing"),
 }
 METRIC = "operand Gbit/s (na+nb bits per product / time)"
 UNIT = "Gbit/s"
@@ -199,6 +201,10 @@ def run_reference(args, world, rank):
         return
     if args.config == 4:
         return run_reference_batch(args)
+    if args.config == 5:
+        print(json.dumps({"impl": "reference", "unavailable": "the serving mix has 2^28-bit operands, minutes per "
+                          "product for the CPU oracle; the reference arm covers configs 1-4 and 6"}), flush=True)
+        return
     cfg = CONFIGS[args.config]
     na, nb = scaled_oracle_workload(cfg["na"], cfg["nb"])
     from oracle import clmul as O
@@ -583,6 +589,67 @@ def serving_requests(count, seed):
     return out
 
 
+def run_reuse(args, world, rank, local):
+    """Products with one fixed operand whose transform is computed once, vs gf2x_mul."""
+    import torch
+    from paper_1803_11301_gb300 import Context, build as lib_build, transform_bits, workspace_bytes
+    lib_build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = CONFIGS[6]
+    na, nb = cfg["na"], cfg["nb"]
+    ctx = Context(local)
+    stream = torch.cuda.current_stream(dev)
+    n = transform_bits(na, nb)
+    b = torch.from_numpy(synth.operand(synth.config_seed(6, 1), nb).view(np.int64)).to(dev)
+    a_list = [torch.from_numpy(synth.operand(synth.config_seed(6, 100 + k), na).view(np.int64)).to(dev)
+              for k in range(4)]
+    c = torch.empty((na + nb - 1 + 63) // 64, dtype=torch.int64, device=dev)
+    ws = torch.empty(workspace_bytes(na, nb), dtype=torch.uint8, device=dev)
+    bhat = ctx.forward_transform(b, nb, n, workspace=ws, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for k in range(args.warmup):
+            flush.fill_(1)
+            fn(a_list[k % len(a_list)])
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        dist_barrier(world)
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k)
+            starts[k].record(stream)
+            fn(a_list[k % len(a_list)])
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        dist_barrier(world)
+        return dist_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    reuse_ms = timed(lambda a: ctx.mul_transformed(a, na, bhat, nb, out=c, workspace=ws, stream=stream))
+    plain_ms = timed(lambda a: ctx.mul(a, na, b, nb, out=c, workspace=ws, stream=stream))
+    clk = clocks.stop()
+    want = ctx.mul(a_list[0], na, b, nb, workspace=ws, stream=stream)
+    got = ctx.mul_transformed(a_list[0], na, bhat, nb, workspace=ws, stream=stream)
+    if not torch.equal(want, got):
+        raise RuntimeError("product with the reused transform differs from gf2x_mul")
+    value = world * (na + nb) * args.steps / (reuse_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": reuse_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "na_bits": na, "nb_bits": nb, "transform_bits": n,
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "plain": {"value": world * (na + nb) * args.steps / (plain_ms / 1e3) / 1e9, "unit": UNIT,
+                      "ms_per_step": plain_ms / args.steps, "how": "gf2x_mul with both operands"},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serving(args, world, rank, local):
     """Continuous batching vs one gf2x_mul per request, same Poisson arrival stream."""
     import torch
@@ -715,6 +782,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.config == 5:
         run_serving(args, world, rank, local)
+    elif args.config == 6:
+        run_reuse(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

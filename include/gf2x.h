@@ -131,6 +131,37 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
                                       const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                                       void *stream);
 
+/* Reusing one operand.  When many products share the operand b, its forward
+ * transform -- lines 4-6 of Alg. 5: BasisCvt, Encode, Butterfly, i.e. the
+ * values B(alpha + u_k) of Eq. 8 at the n_p points of Sigma -- can be
+ * computed once and passed to every product, which then skips them.
+ *
+ * gf2x_transform_bytes(n_bits): bytes of a transform at transform length
+ * n_bits (n_bits / 8, one uint64 per point), 0 unless n_bits is a power of
+ * two with 64 <= n_bits <= 2^37.
+ *
+ * gf2x_forward_transform: bhat (device, gf2x_transform_bytes(n_bits) bytes,
+ *   8-byte aligned, disjoint from b and the workspace) <- the transform of b
+ *   (nb_bits bits, 1 <= nb_bits <= n_bits) at length n_bits.  Use n_bits =
+ *   gf2x_transform_bits(na, nb_bits) for products with na-bit operands; the
+ *   workspace of such a product (gf2x_workspace_bytes(na, nb_bits), or
+ *   3 n_bits/8 + 256 bytes, 256-aligned) suffices.  Asynchronous.
+ *
+ * gf2x_mul_transformed: c = a * b, with b given as bhat = its transform at
+ *   gf2x_transform_bits(na_bits, nb_bits) (the caller keeps bhat consistent
+ *   with b and that length; the library cannot check it).  bhat is only
+ *   read.  Other arguments, sizes and errors as for gf2x_mul; c must not
+ *   overlap bhat.  Both calls replay from a captured CUDA graph from the
+ *   second identical call on, like gf2x_mul.  The paper has no separate
+ *   entry point for this; it is lines 1-10 of Alg. 5 with lines 4-6 done
+ *   ahead of time. */
+GF2X_API size_t gf2x_transform_bytes(uint64_t n_bits);
+GF2X_API gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb_bits, uint64_t n_bits,
+                                            uint64_t *bhat, void *workspace, size_t ws_bytes, void *stream);
+GF2X_API gf2x_status gf2x_mul_transformed(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits, const uint64_t *bhat,
+                                          uint64_t nb_bits, uint64_t *c, void *workspace, size_t ws_bytes,
+                                          void *stream);
+
 /* One product of a batch: c = a * b, pointers and lengths as for gf2x_mul. */
 typedef struct gf2x_job {
     const uint64_t *a;

@@ -40,6 +40,9 @@ ABI_FUNCTIONS = {
     "gf2x_host_workspace_bytes": (_SZ, [_U64, _U64]),
     "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_mul_noalloc": (_ST, [_P, _P, _U64, _P, _U64, _P, _P]),
+    "gf2x_transform_bytes": (_SZ, [_U64]),
+    "gf2x_forward_transform": (_ST, [_P, _P, _U64, _U64, _P, _P, _SZ, _P]),
+    "gf2x_mul_transformed": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_batch_workspace_bytes": (_SZ, [_P, _SZ]),
     "gf2x_mul_batch": (_ST, [_P, _P, _SZ, _P, _SZ, _P]),
     "gf2x_stream_status": (_ST, [_P, _P]),
@@ -185,6 +188,36 @@ class Context:
                                   self._tensor_ptr(out, _words(nc), "out"),
                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                   self._stream(stream)), "gf2x_mul")
+        return out
+
+    def forward_transform(self, b, nb: int, n: int, out=None, workspace=None, stream=None):
+        """The transform of b (lines 4-6 of Alg. 5) at transform length n, for reuse."""
+        if out is None:
+            out = self.empty_words(n // 64)
+        need = 3 * ((n // 8 + 255) // 256 * 256) + 256
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_forward_transform(self._h, self._tensor_ptr(b, _words(nb), "b"), nb, n,
+                                                self._tensor_ptr(out, n // 64, "out"),
+                                                ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                                self._stream(stream)), "gf2x_forward_transform")
+        return out
+
+    def mul_transformed(self, a, na: int, bhat, nb: int, out=None, workspace=None, stream=None):
+        """c = a * b with b given as its transform bhat at transform_bits(na, nb)."""
+        nc = product_bits(na, nb)
+        if out is None:
+            out = self.empty_words(_words(nc))
+        if nc == 0:
+            return out
+        need = workspace_bytes(na, nb)
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_mul_transformed(self._h, self._tensor_ptr(a, _words(na), "a"), na,
+                                              self._tensor_ptr(bhat, transform_bits(na, nb) // 64, "bhat"), nb,
+                                              self._tensor_ptr(out, _words(nc), "out"),
+                                              ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                              self._stream(stream)), "gf2x_mul_transformed")
         return out
 
     def mul_host(self, a, na: int, b, nb: int, out=None, workspace=None, stream=None):

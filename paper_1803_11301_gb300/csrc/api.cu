@@ -252,7 +252,15 @@ struct StageScope {
 // operands, result, workspace and sizes: the second such call captures the
 // kernel sequence on a private stream and every later call launches the graph
 // into the caller's stream (one launch instead of ~15-40).
+// What a cached sequence computes (the arguments are read accordingly).
+enum OpKind {
+    OP_MUL = 0,               // c = a * b
+    OP_MUL_TRANSFORMED = 1,   // c = a * b, b given as its transform at b's pointer
+    OP_FORWARD_TRANSFORM = 2  // c = transform of a (na bits) at length nb
+};
+
 struct GraphEntry {
+    int kind;
     const u64 *a, *b;
     u64 na, nb;
     u64 *c;
@@ -266,7 +274,7 @@ struct GraphEntry {
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
-    struct Key { const u64 *a, *b; u64 na, nb; u64 *c; void *ws; };
+    struct Key { int kind; const u64 *a, *b; u64 na, nb; u64 *c; void *ws; };
     std::vector<Key> seen;              // keys called once, not captured yet
     cudaStream_t cap = nullptr;
     unsigned long long clock = 0;
@@ -338,6 +346,25 @@ gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
     return GF2X_OK;
 }
 
+// Lines 8-10 of Alg. 5 from the low-layer kernel on: top iButterfly layers,
+// Decode, iBasisCvt, store.
+gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
+{
+    const int l = log2_u64(r.n) - 6;
+    const int cnt = r.count;
+    const u64 sd = r.stride;
+    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, r.X, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, r.X, l, r.T, cnt, sd, st)); }
+    // X is free once Decode has read it: the scratch buffer of iBasisCvt
+    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st)); }
+    {
+        StageScope g(ctx, STAGE_STORE, st);
+        if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
+        else TRY(gf2x::store_bits(ctx, r.T, product_bits(r.na, r.nb), r.c, st));
+    }
+    return GF2X_OK;
+}
+
 gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 {
     const int l = log2_u64(r.n) - 6;
@@ -351,22 +378,51 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
         s = forward(ctx, r, 1, r.Y, st);
         if (s != GF2X_OK) return s;
     }
-    u64 *X = r.X, *Y = r.Y;
-    const int cnt = r.count;
-    const u64 sd = r.stride;
     // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
-    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, X, Y, l, cnt, sd, st)); }
-    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, X, Y, l, cnt, sd, st)); }
-    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, X, l, cnt, sd, st)); }
-    { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, X, l, r.T, cnt, sd, st)); }
-    // X is free once Decode has read it: the scratch buffer of iBasisCvt
-    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st)); }
-    {
-        StageScope g(ctx, STAGE_STORE, st);
-        if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
-        else TRY(gf2x::store_bits(ctx, r.T, product_bits(r.na, r.nb), r.c, st));
-    }
+    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, r.X, r.Y, l, r.count, r.stride, st)); }
+    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, r.X, r.Y, l, r.count, r.stride, st)); }
+    return inverse_tail(ctx, r, st);
+}
+
+// Lines 4-6 of Alg. 5 on their own: bhat <- Butterfly(Encode(BasisCvt(b)))
+// at transform length n, for reuse by products with that n.  Workspace as for
+// a product with transform length n: X is BasisCvt's scratch, T the bit array.
+gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n, u64 *bhat, void *ws,
+                                     cudaStream_t st)
+{
+    const int l = log2_u64(n) - 6;
+    const u64 L = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
+    const size_t buf = buffer_bytes(n);
+    u64 *X = (u64 *)ws, *T = (u64 *)((char *)ws + 2 * buf);
+    { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, b, nb, T, n / 64, st)); }
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st)); }
+    { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, bhat, L, 1, 0, 0, st)); }
+    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, bhat, l, false, 1, 0, st)); }
     return GF2X_OK;
+}
+
+// c = a * b with b given as its forward transform bhat (at n = transform
+// length of na x nb): lines 1-3 for a, 7 with bhat, 8-10.
+gf2x_status mul_transformed_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *bhat, u64 nb, u64 *c, void *ws,
+                                   cudaStream_t st)
+{
+    ClassRun r{};
+    r.n = transform_bits(na, nb);
+    r.count = 1;
+    r.La = next_pow2(na) < 64 ? 64 : next_pow2(na);
+    r.a = a; r.na = na; r.nb = nb; r.c = c;
+    const size_t buf = buffer_bytes(r.n);
+    r.X = (u64 *)ws;
+    r.T = (u64 *)((char *)ws + 2 * buf);
+    const int l = log2_u64(r.n) - 6;
+    gf2x_status s = forward(ctx, r, 0, r.X, st);
+    if (s != GF2X_OK) return s;
+    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, r.X, nullptr, l, 1, 0, st)); }
+    {
+        StageScope g(ctx, STAGE_BOTTOM, st);
+        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, (u64 *)bhat, l, 1, 0, st, true));
+    }
+    return inverse_tail(ctx, r, st);
 }
 
 gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
@@ -392,17 +448,26 @@ gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb
     return run_class(ctx, r, st);
 }
 
-// gf2x_mul through the graph cache (falls back to direct launches while a key
+gf2x_status op_device(gf2x_ctx *ctx, int kind, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                      cudaStream_t st)
+{
+    if (kind == OP_MUL_TRANSFORMED) return mul_transformed_device(ctx, a, na, b, nb, c, ws, st);
+    if (kind == OP_FORWARD_TRANSFORM) return forward_transform_device(ctx, a, na, nb, c, ws, st);
+    return mul_device(ctx, a, na, b, nb, c, ws, st);
+}
+
+// A sequence through the graph cache (falls back to direct launches while a key
 // is new, while the caller's stream is itself being captured, or when
 // GF2X_GRAPHS=0 is set in the environment).
-gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws, cudaStream_t st)
+gf2x_status op_graph(gf2x_ctx *ctx, int kind, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                     cudaStream_t st)
 {
     GraphCache *gc = graphs(ctx);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (gc->disabled || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-        return mul_device(ctx, a, na, b, nb, c, ws, st);
+        return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     for (GraphEntry &e : gc->entries) {
-        if (e.a == a && e.b == b && e.na == na && e.nb == nb && e.c == c && e.ws == ws &&
+        if (e.kind == kind && e.a == a && e.b == b && e.na == na && e.nb == nb && e.c == c && e.ws == ws &&
             e.profiling == ctx->profiling) {
             e.stamp = ++gc->clock;
             if (cudaGraphLaunch(e.exec, st) != cudaSuccess) return GF2X_ECUDA;
@@ -415,7 +480,8 @@ gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
     bool repeat = false;
     for (size_t k = 0; k < gc->seen.size(); ++k) {
         const GraphCache::Key &key = gc->seen[k];
-        if (key.a == a && key.b == b && key.na == na && key.nb == nb && key.c == c && key.ws == ws) {
+        if (key.kind == kind && key.a == a && key.b == b && key.na == na && key.nb == nb && key.c == c &&
+            key.ws == ws) {
             repeat = true;
             gc->seen.erase(gc->seen.begin() + (long)k);
             break;
@@ -423,21 +489,22 @@ gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
     }
     if (!repeat) {
         if (gc->seen.size() >= 64) gc->seen.erase(gc->seen.begin());
-        gc->seen.push_back({a, b, na, nb, c, ws});
-        return mul_device(ctx, a, na, b, nb, c, ws, st);
+        gc->seen.push_back({kind, a, b, na, nb, c, ws});
+        return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     }
     // second call with this key: capture, instantiate, launch
     if (!gc->cap && cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking) != cudaSuccess)
-        return mul_device(ctx, a, na, b, nb, c, ws, st);
+        return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     GraphEntry e{};
+    e.kind = kind;
     e.a = a; e.b = b; e.na = na; e.nb = nb; e.c = c; e.ws = ws; e.profiling = ctx->profiling;
     unsigned long long before[STAGE_COUNT];
     for (int k = 0; k < STAGE_COUNT; ++k) before[k] = ctx->launches[k];
     Profiler *p = profiler(ctx);
     if (cudaStreamBeginCapture(gc->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return mul_device(ctx, a, na, b, nb, c, ws, st);
+        return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     p->capture = &e.recs;
-    gf2x_status s = mul_device(ctx, a, na, b, nb, c, ws, gc->cap);
+    gf2x_status s = op_device(ctx, kind, a, na, b, nb, c, ws, gc->cap);
     p->capture = nullptr;
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(gc->cap, &graph);
@@ -449,14 +516,14 @@ gf2x_status mul_graph(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
         if (graph) cudaGraphDestroy(graph);
         for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         cudaGetLastError();
-        return s != GF2X_OK ? s : mul_device(ctx, a, na, b, nb, c, ws, st);
+        return s != GF2X_OK ? s : op_device(ctx, kind, a, na, b, nb, c, ws, st);
     }
     ce = cudaGraphInstantiate(&e.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
         for (Rec &r : e.recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         cudaGetLastError();
-        return mul_device(ctx, a, na, b, nb, c, ws, st);
+        return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     }
     if (gc->entries.size() >= kMaxGraphs) {       // evict the least recently used
         size_t old = 0;
@@ -732,7 +799,49 @@ gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64
         return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GF2X_ECUDA;
-    return mul_graph(ctx, a, na, b, nb, c, ws, (cudaStream_t)stream);
+    return op_graph(ctx, OP_MUL, a, na, b, nb, c, ws, (cudaStream_t)stream);
+}
+
+size_t gf2x_transform_bytes(uint64_t n)
+{
+    return valid_n(n) ? (size_t)(n / 8) : 0;
+}
+
+gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb, uint64_t n, uint64_t *bhat,
+                                   void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n(n) || nb == 0 || nb > n) return GF2X_EINVAL;
+    if (!b || !bhat || !ws || !aligned8(b) || !aligned8(bhat) || ((uintptr_t)ws % kAlign)) return GF2X_EINVAL;
+    const size_t need = 3 * buffer_bytes(n) + kAlign;
+    if (ws_bytes < need) return GF2X_ENOSPACE;
+    const size_t tb = (size_t)(n / 8);
+    if (overlap(bhat, tb, b, (size_t)((nb + 63) / 64) * 8) || overlap(bhat, tb, ws, need)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    return op_graph(ctx, OP_FORWARD_TRANSFORM, b, nb, nullptr, n, bhat, ws, (cudaStream_t)stream);
+}
+
+gf2x_status gf2x_mul_transformed(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *bhat, uint64_t nb,
+                                 uint64_t *c, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    const u64 nc = product_bits(na, nb);
+    if (!nc) return GF2X_OK;
+    const u64 n = transform_bits(na, nb);
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!a || !bhat || !c || !ws || !aligned8(a) || !aligned8(bhat) || !aligned8(c) || ((uintptr_t)ws % kAlign))
+        return GF2X_EINVAL;
+    const size_t need = gf2x_workspace_bytes(na, nb);
+    if (ws_bytes < need) return GF2X_ENOSPACE;
+    const size_t cb = (size_t)((nc + 63) / 64) * 8;
+    if (overlap(c, cb, a, (size_t)((na + 63) / 64) * 8) || overlap(c, cb, bhat, (size_t)(n / 8)) ||
+        overlap(c, cb, ws, need) || overlap(bhat, (size_t)(n / 8), ws, need))
+        return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    return op_graph(ctx, OP_MUL_TRANSFORMED, a, na, bhat, nb, c, ws, (cudaStream_t)stream);
 }
 
 size_t gf2x_host_workspace_bytes(uint64_t na, uint64_t nb)
@@ -765,7 +874,7 @@ gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, co
     u64 *dc = (u64 *)((char *)db + round_up(bb));
     TRY(cudaMemcpyAsync(da, a_host, ab, cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(db, b_host, bb, cudaMemcpyHostToDevice, st));
-    gf2x_status s = mul_graph(ctx, da, na, db, nb, dc, ws, st);
+    gf2x_status s = op_graph(ctx, OP_MUL, da, na, db, nb, dc, ws, st);
     if (s != GF2X_OK) return s;
     TRY(cudaMemcpyAsync(c_host, dc, cb, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));

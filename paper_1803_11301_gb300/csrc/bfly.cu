@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
 }
 
 // -------------------------------------------------------------- bottom tile
-enum BottomMode { BOTTOM_FWD = 0, BOTTOM_INV = 1, BOTTOM_FUSED = 2 };
+// BOTTOM_FUSED: Y holds the top-layer output of the second forward transform;
+// BOTTOM_FUSED_PRE: Y already holds a complete forward transform (a reused
+// operand), so only X's low layers run before the pointwise product.
+enum BottomMode { BOTTOM_FWD = 0, BOTTOM_INV = 1, BOTTOM_FUSED = 2, BOTTOM_FUSED_PRE = 3 };
 
 // One layer i (< bt) on a tile held in shared memory.  ctop = v_{l+32-i} +
 // Cantor((tile base) >> i); the block of local start s_lo adds Cantor(s_lo >> i).
@@ -244,7 +247,8 @@ __global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, 
     X += (u64)blockIdx.y * stride;                      // job of a batch
     if (Y) Y += (u64)blockIdx.y * stride;
     const int T = 1 << bt;
-    const bool fused = mode == BOTTOM_FUSED;
+    const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;   // Y's tile is loaded
+    const bool fwd_b = mode == BOTTOM_FUSED;                               // and transformed here
     u64 *a = sm;
     u64 *b = fused ? sm + T : nullptr;
     u64 *tabs = sm + (fused ? 2 : 1) * T;
@@ -257,11 +261,11 @@ __global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, 
     if (mode != BOTTOM_INV) {
         for (int i = bt - 1; i >= 0; --i) {
             if (i >= kTableMin) {
-                table_layer<CHUNK>(a, b, bt, i, l, base, cvt, vb, tabs, false);
+                table_layer<CHUNK>(a, fwd_b ? b : nullptr, bt, i, l, base, cvt, vb, tabs, false);
             } else {
                 const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
                 tile_layer(a, bt, i, ctop, cvt, false);
-                if (fused) tile_layer(b, bt, i, ctop, cvt, false);
+                if (fwd_b) tile_layer(b, bt, i, ctop, cvt, false);
                 __syncthreads();
             }
         }
@@ -300,7 +304,7 @@ constexpr int kBottomThreadsLarge = 256, kBottomChunkLarge = 16;
 void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride, cudaStream_t st)
 {
     const u64 tiles = 1ull << (l - bt);
-    const bool fused = mode == BOTTOM_FUSED;
+    const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;
     const dim3 grid((unsigned)tiles, count);
     if (tiles * (u64)count < 4 * (u64)ctx->num_sms)
         k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall><<<grid, kBottomThreadsSmall,
@@ -394,11 +398,13 @@ cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count
 
 // Bottom layers of both forward transforms, the pointwise product and the
 // bottom layers of the inverse: X <- low layers of iButterfly(fwd(X) * fwd(Y)).
-cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st)
+// With y_transformed, Y is already a complete forward transform.
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
+                                   bool y_transformed)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    launch_bottom(ctx, X, Y, l, bt, BOTTOM_FUSED, count, stride, st);
+    launch_bottom(ctx, X, Y, l, bt, y_transformed ? BOTTOM_FUSED_PRE : BOTTOM_FUSED, count, stride, st);
     return cudaGetLastError();
 }
 

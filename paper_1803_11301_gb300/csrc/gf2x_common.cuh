@@ -143,7 +143,8 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
 cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st);
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st);
 cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
-cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
+                                   bool y_transformed = false);
 cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
 cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u64 stride, u64 dst_words, int count,
                       cudaStream_t st);

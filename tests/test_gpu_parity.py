@@ -316,3 +316,31 @@ def test_serving_results_same_alone_and_in_the_mix(ctx):
         alone = ctx.mul(r.a, r.na, r.b, r.nb)
         nc = r.na + r.nb - 1
         assert torch.equal(r.out[: (nc + 63) // 64], alone), r.tag
+
+
+# ------------------------------------------------------------ reused operand
+@pytest.mark.parametrize("na,nb", [(100, 5000), (1 << 16, 1 << 16), (70001, 3333), (1 << 20, 1 << 18), (64, 64)])
+def test_reused_operand_transform(ctx, na, nb):
+    # lines 4-6 of Alg. 5 once for b (gf2x_forward_transform), then products
+    # with several a of the same transform length (gf2x_mul_transformed)
+    from paper_1803_11301_gb300 import transform_bits
+    b = synth.operand(synth.config_seed(9, nb), nb)
+    n = transform_bits(na, nb)
+    bhat = ctx.forward_transform(dev(b), nb, n)
+    for k in range(3):
+        a = synth.operand(synth.config_seed(9, 1000 + k), na)
+        for _ in range(2):                            # second call replays the captured graph
+            got = host(ctx.mul_transformed(dev(a), na, bhat, nb))
+            assert np.array_equal(got, O.mul(a, na, b, nb)), (na, nb, k)
+
+
+def test_forward_transform_is_evaluation_at_sigma(ctx):
+    # the reusable transform is the forward path: B(alpha + u_k) (Eq. 8)
+    from paper_1803_11301_gb300 import transform_bits
+    nb = 70001
+    n = transform_bits(nb, nb)
+    l = n.bit_length() - 1 - 6
+    b = synth.operand(synth.config_seed(9, 7), nb)
+    y = host(ctx.forward_transform(dev(b), nb, n))
+    for k in sorted({0, 1, (1 << l) - 1} | {rng.randrange(1 << l) for _ in range(5)}):
+        assert int(y[k]) == O.eval_at(synth.mask_tail(b.copy(), nb), nb, S.sigma_point(l, k)), k
