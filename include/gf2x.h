@@ -94,7 +94,12 @@ GF2X_API size_t gf2x_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
  * most 16 are kept per context, least recently used dropped); the contents of
  * the buffers may change between calls.  Set GF2X_GRAPHS=0 in the environment
  * before creating the context to launch kernels one by one instead.  A context
- * is not thread-safe: serialise calls that share it. */
+ * is not thread-safe: serialise calls that share it.
+ * First use of a size: some kernels have variants that differ only in speed
+ * (threads per block, rows per window); the first call that meets a new launch
+ * shape times them on the workspace's free buffers and keeps the fastest, so
+ * that call waits for its stream.  Set GF2X_TUNE=0 in the environment before
+ * creating the context to use built-in defaults without measuring. */
 GF2X_API gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
                      const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                      void *workspace, size_t ws_bytes, void *stream);

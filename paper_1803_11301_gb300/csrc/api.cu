@@ -380,7 +380,11 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
     }
     // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
     { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, r.X, r.Y, l, r.count, r.stride, st)); }
-    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::butterfly_bottom_fused(ctx, r.X, r.Y, l, r.count, r.stride, st)); }
+    // T is free between Encode and Decode: the tuner's scratch for the low-layer kernel
+    {
+        StageScope g(ctx, STAGE_BOTTOM, st);
+        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, r.Y, l, r.count, r.stride, st, false, r.T));
+    }
     return inverse_tail(ctx, r, st);
 }
 
@@ -397,7 +401,7 @@ gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n,
     { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, b, nb, T, n / 64, st)); }
     { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st)); }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, bhat, L, 1, 0, 0, st)); }
-    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, bhat, l, false, 1, 0, st)); }
+    { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, bhat, l, false, 1, 0, st, T)); }
     return GF2X_OK;
 }
 
@@ -420,7 +424,7 @@ gf2x_status mul_transformed_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u6
     { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, r.X, nullptr, l, 1, 0, st)); }
     {
         StageScope g(ctx, STAGE_BOTTOM, st);
-        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, (u64 *)bhat, l, 1, 0, st, true));
+        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, (u64 *)bhat, l, 1, 0, st, true, r.T));
     }
     return inverse_tail(ctx, r, st);
 }
@@ -686,10 +690,12 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     ctx->prof = new (std::nothrow) Profiler();
     ctx->graphs = new (std::nothrow) GraphCache();
     ctx->batch_graphs = new (std::nothrow) BatchCache();
-    if (!ctx->prof || !ctx->graphs || !ctx->batch_graphs) {
+    ctx->tuner = gf2x::tuner_create();
+    if (!ctx->prof || !ctx->graphs || !ctx->batch_graphs || !ctx->tuner) {
         delete profiler(ctx);
         delete graphs(ctx);
         delete (BatchCache *)ctx->batch_graphs;
+        gf2x::tuner_destroy(ctx->tuner);
         delete ctx;
         return GF2X_ENOMEM;
     }
@@ -701,6 +707,7 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
         delete profiler(ctx);
         delete graphs(ctx);
         delete (BatchCache *)ctx->batch_graphs;
+        gf2x::tuner_destroy(ctx->tuner);
         delete ctx;
         return st;
     };
@@ -767,6 +774,7 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx)
             if (r.pooled) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         delete p;
     }
+    gf2x::tuner_destroy(ctx->tuner);
     cudaFree(ctx->d_tables);
     cudaFree(ctx->d_status);
     delete ctx;

@@ -301,18 +301,36 @@ size_t bottom_smem(int bt, bool fused, int chunk)
 constexpr int kBottomThreadsSmall = 512, kBottomChunkSmall = 32;
 constexpr int kBottomThreadsLarge = 256, kBottomChunkLarge = 16;
 
-void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride, cudaStream_t st)
+// shape 1: the small-count shape, 0: the large-count one
+cudaError_t launch_bottom_shape(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride,
+                                int shape, cudaStream_t st)
 {
-    const u64 tiles = 1ull << (l - bt);
     const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;
-    const dim3 grid((unsigned)tiles, count);
-    if (tiles * (u64)count < 4 * (u64)ctx->num_sms)
+    const dim3 grid((unsigned)(1ull << (l - bt)), count);
+    if (shape)
         k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall><<<grid, kBottomThreadsSmall,
             bottom_smem(bt, fused, kBottomChunkSmall), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
     else
         k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge><<<grid, kBottomThreadsLarge,
             bottom_smem(bt, fused, kBottomChunkLarge), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
     count_launch(ctx);
+    return cudaGetLastError();
+}
+
+// The shape measured by the tuner on `scratch` (a free buffer laid out like X;
+// Y, when the mode reads it, is only read), or the default without one.
+void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride, u64 *scratch,
+                   cudaStream_t st)
+{
+    const u64 tiles = 1ull << (l - bt);
+    int shape = tiles * (u64)count < 4 * (u64)ctx->num_sms ? 1 : 0;
+    if (scratch) {
+        static const int cands[2] = {1, 0};
+        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, ((tiles * (u64)count) << 2) | (u64)mode, cands, 2, shape,
+                            [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, st); },
+                            st);
+    }
+    launch_bottom_shape(ctx, X, Y, l, bt, mode, count, stride, shape, st);
 }
 
 template <int M, bool INV>
@@ -373,7 +391,8 @@ void configure()
 
 // Forward (or inverse) Butterfly of `count` transforms of 2^l points each,
 // `stride` words apart.
-cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st)
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st,
+                      u64 *scratch)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
@@ -382,7 +401,7 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
         if (e != cudaSuccess) return e;
     }
     if (bt > 0) {
-        launch_bottom(ctx, x, nullptr, l, bt, inverse ? BOTTOM_INV : BOTTOM_FWD, count, stride, st);
+        launch_bottom(ctx, x, nullptr, l, bt, inverse ? BOTTOM_INV : BOTTOM_FWD, count, stride, scratch, st);
     }
     if (inverse) return top_passes(ctx, x, nullptr, l, bt, true, count, stride, st);
     return cudaGetLastError();
@@ -400,11 +419,11 @@ cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count
 // bottom layers of the inverse: X <- low layers of iButterfly(fwd(X) * fwd(Y)).
 // With y_transformed, Y is already a complete forward transform.
 cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
-                                   bool y_transformed)
+                                   bool y_transformed, u64 *scratch)
 {
     configure();
     const int bt = l < kBottom ? l : kBottom;
-    launch_bottom(ctx, X, Y, l, bt, y_transformed ? BOTTOM_FUSED_PRE : BOTTOM_FUSED, count, stride, st);
+    launch_bottom(ctx, X, Y, l, bt, y_transformed ? BOTTOM_FUSED_PRE : BOTTOM_FUSED, count, stride, scratch, st);
     return cudaGetLastError();
 }
 

@@ -616,11 +616,25 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
                                  u64 stride, cudaStream_t st)
 {
     const int m = K - 16;
-    // Layers in the window kernel: its cost grows faster than linearly with
-    // the depth (the halo and the rows per block double with each layer), so
-    // deep windows only pay while the array sits in L2.  Measured on GB300:
-    // 8 layers for K <= 25, 7 above (the remaining layers as wide steps).
-    const int cap = K <= 25 ? 8 : 7;
+    // Layers in the window kernel (at most 8; the rest are wide steps): its
+    // cost grows faster than linearly with the depth (the halo and the rows
+    // per block double with each layer), so deep windows pay most while the
+    // array sits in L2.  The tuner compares depths 6, 7 and 8 on the layers
+    // below 8 (window from bits into scratch, then the remaining wide steps
+    // in place on scratch); the default found on GB300 is 8 for K <= 25 and 7
+    // above.
+    int cap = K <= 25 ? 8 : 7;
+    if (m > 6) {
+        static const int cands[3] = {6, 7, 8};
+        const int top = m < 8 ? m : 8;
+        cap = tune_choice(ctx, TUNE_WINDOW_DEPTH, ((u64)K << 33) | ((u64)count << 1) | (inverse ? 1u : 0u), cands,
+                          top - 5, cap, [&](int c) -> cudaError_t {
+                              std::vector<Step> w;
+                              for (int k = top - 1; k >= c; --k) w.push_back({1ull << (16 + k), 1ull << k});
+                              TRY_CUDA(taylor_window_launch(ctx, scratch, bits, L, c, inverse, count, stride, st));
+                              return run_steps_generic(ctx, scratch, scratch, L, w, inverse, count, stride, st);
+                          }, st);
+    }
     const int mw = m < cap ? m : cap;
     std::vector<Step> taylor_wide, outer_taylor;
     for (int k = m - 1; k >= mw; --k) taylor_wide.push_back({1ull << (16 + k), 1ull << k});
@@ -638,9 +652,9 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
             TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, false, count, stride, st));
             TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, 8, kUnitWordsLog, false, count, stride, st));
         }
-        return basis_cvt_unit16(ctx, bits, L, false, count, stride, st);
+        return basis_cvt_unit16(ctx, bits, L, false, count, stride, scratch, st);
     }
-    TRY_CUDA(basis_cvt_unit16(ctx, bits, L, true, count, stride, st));
+    TRY_CUDA(basis_cvt_unit16(ctx, bits, L, true, count, stride, scratch, st));
     if (m <= 9) {
         TRY_CUDA(basis_cvt_outer(ctx, scratch, bits, L, m, kUnitWordsLog, true, count, stride, st));
     } else {
@@ -669,12 +683,12 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, 
     const bool unit16 = K >= 16;
     if (unit16) steps.resize(steps.size() - 32);
     if (inverse) {
-        if (unit16) TRY_CUDA(basis_cvt_unit16(ctx, bits, L, true, count, stride, st));
+        if (unit16) TRY_CUDA(basis_cvt_unit16(ctx, bits, L, true, count, stride, scratch, st));
         return run_steps_generic(ctx, bits, bits, L, std::vector<Step>(steps.rbegin(), steps.rend()), true, count,
                                  stride, st);
     }
     TRY_CUDA(run_steps_generic(ctx, bits, bits, L, steps, false, count, stride, st));
-    return unit16 ? basis_cvt_unit16(ctx, bits, L, false, count, stride, st) : cudaSuccess;
+    return unit16 ? basis_cvt_unit16(ctx, bits, L, false, count, stride, scratch, st) : cudaSuccess;
 }
 
 cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st)

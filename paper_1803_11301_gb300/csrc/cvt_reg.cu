@@ -467,11 +467,19 @@ cudaError_t basis_cvt_unit16_r(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, in
     return cudaGetLastError();
 }
 
-cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st)
+// R measured by the tuner on `scratch` (a buffer laid out like bits, free),
+// or without one the default found on GB300: R = 8 up to 512 blocks (2^25
+// bits), R = 32 from 1024.
+cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
+                             cudaStream_t st)
 {
-    // measured on GB300: R = 8 up to 512 blocks (2^25 bits), R = 32 from 1024
     const u64 blocks = (L >> 16) * (u64)count;
-    const int R = blocks <= 4 * (u64)ctx->num_sms ? 8 : 32;
+    int R = blocks <= 4 * (u64)ctx->num_sms ? 8 : 32;
+    if (scratch) {
+        static const int cands[3] = {8, 16, 32};
+        R = tune_choice(ctx, TUNE_UNIT16_R, (blocks << 1) | (inverse ? 1u : 0u), cands, 3, R,
+                        [&](int r) { return basis_cvt_unit16_r(ctx, scratch, L, inverse, count, stride, r, st); }, st);
+    }
     return basis_cvt_unit16_r(ctx, bits, L, inverse, count, stride, R, st);
 }
 

@@ -9,6 +9,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 
 #include <cuda_runtime.h>
 
@@ -113,6 +114,7 @@ struct gf2x_ctx {
     void *prof;                         // event pool, see api.cu
     void *graphs;                       // CUDA graph cache of gf2x_mul, see api.cu
     void *batch_graphs;                 // CUDA graph cache of gf2x_mul_batch
+    void *tuner;                        // measured launch-shape choices, see tune.cu
 };
 
 // Count one kernel launch against the current stage.
@@ -122,6 +124,16 @@ inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] +
 // All enqueue on `st` and return cudaGetLastError().
 namespace gf2x {
 
+// Autotuner (tune.cu).  Knobs: the choices it measures.
+enum TuneKnob { TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3 };
+void *tuner_create();
+void tuner_destroy(void *t);
+// The stored choice for (knob, key); else, when measuring is possible, runs
+// run(candidate) on `st` for every candidate, stores and returns the fastest;
+// else `fallback`.
+int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, int fallback,
+                const std::function<cudaError_t(int)> &run, cudaStream_t st);
+
 // Batched forms: `count` jobs whose buffers are `stride` words apart
 // (count = 1, stride = 0 for a single product).
 // BasisCvt (or iBasisCvt) in place on bits.  `scratch`, if not null, is a
@@ -130,7 +142,9 @@ namespace gf2x {
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
                       cudaStream_t st);
 // BasisCvt inside every 2^16-bit block of an L-bit array (L a multiple of 2^16).
-cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, cudaStream_t st);
+// scratch (nullable): a free buffer laid out like bits, for the tuner.
+cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
+                             cudaStream_t st);
 // Outer BasisCvt of length 2^M (2 <= M <= 9) on units of 2^ulog words, applied
 // to every chunk of 2^M units of an L-bit array, read from src (which may be
 // bits) and written to bits.
@@ -141,10 +155,12 @@ cudaError_t wait_timeout_probe(gf2x_ctx *ctx, GridSync *gs, cudaStream_t st);
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
                    u64 out_stride, cudaStream_t st);
 cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st);
-cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st);
+// scratch (nullable): a free buffer of the transform's size, for the tuner.
+cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st,
+                      u64 *scratch = nullptr);
 cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
 cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
-                                   bool y_transformed = false);
+                                   bool y_transformed = false, u64 *scratch = nullptr);
 cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
 cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u64 stride, u64 dst_words, int count,
                       cudaStream_t st);
