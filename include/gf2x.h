@@ -104,10 +104,12 @@ GF2X_API gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits
                      const uint64_t *b, uint64_t nb_bits, uint64_t *c,
                      void *workspace, size_t ws_bytes, void *stream);
 
-/* The same product with HOST operands and result: copies a and b into the
- * device workspace, runs gf2x_mul, copies c back and waits for the stream.
- * Synchronous.  Host buffers may be pageable; pinned memory is faster.
- * The workspace must hold gf2x_host_workspace_bytes(na, nb) bytes. */
+/* The same product with HOST operands and result, synchronous.  Page-locked
+ * (pinned or registered) buffers are read and written by the product's load
+ * and store kernels directly over the CPU-GPU link; pageable buffers are
+ * copied into the device workspace and the result copied back.  Either way
+ * the call returns once c holds the product.  The workspace must hold
+ * gf2x_host_workspace_bytes(na, nb) bytes. */
 GF2X_API size_t gf2x_host_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
 GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na_bits,
                           const uint64_t *b_host, uint64_t nb_bits, uint64_t *c_host,

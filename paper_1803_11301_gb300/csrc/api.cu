@@ -874,6 +874,25 @@ gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, co
     DeviceGuard g(ctx->device);
     if (!g.ok) return GF2X_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    // Page-locked host buffers are read and written by the load and store
+    // kernels themselves (over the CPU-GPU link, no staging copies); pageable
+    // ones are copied through the workspace.
+    auto device_view = [](const void *p) -> const void * {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    const u64 *va = (const u64 *)device_view(a_host), *vb = (const u64 *)device_view(b_host);
+    u64 *vc = (u64 *)device_view(c_host);
+    if (va && vb && vc) {
+        gf2x_status s = op_graph(ctx, OP_MUL, va, na, vb, nb, vc, ws, st);
+        if (s != GF2X_OK) return s;
+        TRY(cudaStreamSynchronize(st));
+        return GF2X_OK;
+    }
     const size_t base = gf2x_workspace_bytes(na, nb);
     const size_t ab = (size_t)((na + 63) / 64) * 8, bb = (size_t)((nb + 63) / 64) * 8,
                  cb = (size_t)((nc + 63) / 64) * 8;

@@ -214,6 +214,24 @@ def test_host_entry_point(ctx):
         assert np.array_equal(ctx.mul_host(a, na, b, nb), O.mul(a, na, b, nb))
 
 
+def test_host_entry_point_pinned_buffers(ctx):
+    # page-locked host buffers: the load and store kernels use them directly
+    import torch
+    for na, nb in [(1000, 77), (1 << 18, 1 << 17), (1 << 20, 1 << 20)]:
+        nc = na + nb - 1
+        pa = torch.zeros((na + 63) // 64, dtype=torch.int64).pin_memory()
+        pb = torch.zeros((nb + 63) // 64, dtype=torch.int64).pin_memory()
+        pc = torch.zeros((nc + 63) // 64, dtype=torch.int64).pin_memory()
+        va, vb, vc = (t.numpy().view(np.uint64) for t in (pa, pb, pc))
+        for k in range(2):                          # the second call replays the captured graph
+            a = synth.operand(synth.config_seed(10, 2 * k + na), na)
+            b = synth.operand(synth.config_seed(10, 2 * k + nb + 1), nb)
+            va[:] = a
+            vb[:] = b
+            ctx.mul_host(va, na, vb, nb, out=vc)
+            assert np.array_equal(vc, O.mul(a, na, b, nb)), (na, nb, k)
+
+
 # --------------------------------------------------------------- errors
 def test_bounded_wait_reports_timeout(ctx):
     # a device-side wait that can never complete gives up and reports GF2X_ETIMEOUT
