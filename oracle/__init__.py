@@ -14,6 +14,9 @@ Modules
               Encode / Decode (Alg. 4), Butterfly / iButterfly (Alg. 2), the
               pointwise product, plus the definitions used to pin them
               (evaluation at the Frobenius partition, Eq. 7).
+``m128``      The same method with m = 128 (Sec. 3 for general m, Sec. 4.3):
+              GF(2^128) = GF(2)[x]/(x^128+x^7+x^2+x+1), its Cantor basis,
+              Sigma = v_{l+64} + V_l, the 128-row Encode, Butterfly and Alg. 5.
 ``clmul``     The plain carry-less product (the definition the whole method
               must reproduce, Sec. 2.1) and the randomised modular checker,
               backed by the portable C code in ``oracle.c``.
