@@ -51,6 +51,10 @@ CONFIGS = {
                  "5% with one operand of exactly 2^28 bits, continuous batching over 3 streams"),
     6: dict(na=1 << 24, nb=1 << 24, name="reused operand: 2^24 x 2^24-bit products a_k * b with one fixed b, "
                                         "b's transform computed once (gf2x_forward_transform) outside the timing"),
+    7: dict(na=1 << 24, nb=1 << 24, field=128,
+            name="single product 2^24 x 2^24 bits, uniform random, GF(2^128) points (gf2x_mul_m128)"),
+    8: dict(na=1 << 30, nb=1 << 30, field=128,
+            name="single product 2^30 x 2^30 bits, uniform random, GF(2^128) points (gf2x_mul_m128)"),
 }
 METRIC = "operand Gbit/s (na+nb bits per product / time)"
 UNIT = "Gbit/s"
@@ -67,14 +71,18 @@ NUM_SMS = 152
 # shared-memory port, 128 B per SM-clock: at most 1 product per SM per clock.
 PRODUCTS_PER_SM_CLOCK = 1.0
 BOTTOM_LAYERS = 11            # low layers done by the fused bottom kernel
+# GF(2^128) points: the table product reads 32 windows x 16 B = 512 B of
+# shared memory, so at most 1/4 product per SM per clock; 10 bottom layers.
+PRODUCTS_PER_SM_CLOCK_128 = 0.25
+BOTTOM_LAYERS_128 = 10
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a stage's
 # kernel, keyed by (stage, na, nb), from one capture of the same workload
 # (profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md gives both captures).
 # An entry is removed when its kernel changes; a missing entry reports null.
 TRAFFIC_BYTES_PER_LAUNCH = {
-    ("bottom_fused", 1 << 24, 1 << 24): 8426240 + 0,
-    ("bottom_fused", 1 << 30, 1 << 30): 536919552 + 224388864,
+    ("bottom_fused", 1 << 24, 1 << 24, 64): 8426240 + 0,
+    ("bottom_fused", 1 << 30, 1 << 30, 64): 536919552 + 224388864,
 }
 
 
@@ -265,13 +273,13 @@ def run_reference_batch(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def stage_work(stage, na, nb, n, products):
+def stage_work(stage, na, nb, n, products, field=64):
     """Algorithmic work of one stage over `products` products: (amount, kind).
 
-    kind "mul": GF(2^64) products (one per butterfly); kind "hbm": bytes."""
-    l = n.bit_length() - 1 - 6
+    kind "mul": GF(2^m) products (one per butterfly); kind "hbm": bytes."""
+    l = n.bit_length() - 1 - (7 if field == 128 else 6)
     n_p = 1 << l
-    bt = min(BOTTOM_LAYERS, l)
+    bt = min(BOTTOM_LAYERS_128 if field == 128 else BOTTOM_LAYERS, l)
     fw = 2                         # two forward transforms
     la = max(64, 1 << max(0, (na - 1).bit_length()))
     lb = max(64, 1 << max(0, (nb - 1).bit_length()))
@@ -307,6 +315,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(dev)
     cfg = CONFIGS[args.config]
     na, nb = cfg["na"], cfg["nb"]
+    field = cfg.get("field", 64)
     nc = na + nb - 1
     ctx = Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -316,12 +325,15 @@ def run_gpu(args, world, rank, local):
     a = torch.from_numpy(a_h.view(np.int64)).to(dev)
     b = torch.from_numpy(b_h.view(np.int64)).to(dev)
     c = torch.empty((nc + 63) // 64, dtype=torch.int64, device=dev)
-    from paper_1803_11301_gb300 import workspace_bytes, host_workspace_bytes
-    ws = torch.empty(max(workspace_bytes(na, nb), host_workspace_bytes(na, nb)), dtype=torch.uint8, device=dev)
+    from paper_1803_11301_gb300 import workspace_bytes, host_workspace_bytes, m128_workspace_bytes
+    ws_bytes = m128_workspace_bytes(na, nb) if field == 128 else max(workspace_bytes(na, nb),
+                                                                      host_workspace_bytes(na, nb))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    mul = ctx.mul_m128 if field == 128 else ctx.mul
 
     def step():
-        ctx.mul(a, na, b, nb, out=c, workspace=ws, stream=stream)
+        mul(a, na, b, nb, out=c, workspace=ws, stream=stream)
 
     # Two timed regions of K steps each, both with warm-up, L2 flush and CUDA
     # events on the launching stream: (1) plain, for `value`; (2) with the
@@ -371,15 +383,28 @@ def run_gpu(args, world, rank, local):
         b_pin = torch.from_numpy(b_h.view(np.int64)).pin_memory()
         c_pin = torch.empty((nc + 63) // 64, dtype=torch.int64).pin_memory()
         an, bn, cn = (t.numpy().view(np.uint64) for t in (a_pin, b_pin, c_pin))
+
+        def host_step():
+            if field == 128:
+                # pinned host operands copied in, gf2x_mul_m128, product copied out, on one stream
+                with torch.cuda.stream(stream):
+                    a.copy_(a_pin, non_blocking=True)
+                    b.copy_(b_pin, non_blocking=True)
+                    ctx.mul_m128(a, na, b, nb, out=c, workspace=ws, stream=stream)
+                    c_pin.copy_(c, non_blocking=True)
+                stream.synchronize()
+            else:
+                ctx.mul_host(an, na, bn, nb, out=cn, workspace=ws, stream=stream)   # synchronous
+
         for _ in range(max(1, args.warmup)):
-            ctx.mul_host(an, na, bn, nb, out=cn, workspace=ws, stream=stream)
+            host_step()
         e2e_times = []
         dist_barrier(world)
         for k in range(args.steps):
             flush.fill_(k)
             torch.cuda.synchronize(dev)
             t = time.perf_counter()
-            ctx.mul_host(an, na, bn, nb, out=cn, workspace=ws, stream=stream)   # synchronous
+            host_step()
             e2e_times.append(time.perf_counter() - t)
         e2e_total = dist_max(sum(e2e_times), world)
         h2d = ((na + 63) // 64 + (nb + 63) // 64) * 8
@@ -391,26 +416,28 @@ def run_gpu(args, world, rank, local):
 
     # roofline of the dominant stage
     hbm_peak, sm_max_mhz, peak_src = load_peaks()
-    n = 1 << max(6, (nc - 1).bit_length())
+    n = 1 << max(7 if field == 128 else 6, (nc - 1).bit_length())
     stages = {}
     for name, (ms, nl) in prof.items():
-        work, kind = stage_work(name, na, nb, n, args.steps)
+        work, kind = stage_work(name, na, nb, n, args.steps, field)
         stages[name] = {"ms": ms / args.steps, "launches_per_step": nl / args.steps, "bound": kind,
                         "work_per_step": work / args.steps}
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
     if d["bound"] == "mul":
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
-        peak = NUM_SMS * PRODUCTS_PER_SM_CLOCK * sm_max_mhz * 1e6 / 1e9
+        per_clock = PRODUCTS_PER_SM_CLOCK_128 if field == 128 else PRODUCTS_PER_SM_CLOCK
+        peak = NUM_SMS * per_clock * sm_max_mhz * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s", "frac": achieved / peak,
-                "peak_source": (f"derived: {NUM_SMS} SMs x {sm_max_mhz:.0f} MHz x {PRODUCTS_PER_SM_CLOCK:g} GF(2^64) "
+                "peak_source": (f"derived: {NUM_SMS} SMs x {sm_max_mhz:.0f} MHz x {per_clock:g} GF(2^{field}) "
                                 "product per SM-clock (shared-memory port bound of the table product)"),
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb)), "kernel_stage": dom,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field)), "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
     else:
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb)), "kernel_stage": dom,
+                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field)),
+                "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
 
     compulsory = ((na + 63) // 64 + (nb + 63) // 64 + (nc + 63) // 64) * 8
@@ -418,7 +445,7 @@ def run_gpu(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "us_per_product": 1e3 * ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "na_bits": na, "nb_bits": nb, "transform_bits": n,
+            "config": {"workload": cfg["name"], "na_bits": na, "nb_bits": nb, "transform_bits": n, "field_bits": field,
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"{world} independent replica(s)"},
             "hbm_compulsory": {"bytes_per_product": compulsory,

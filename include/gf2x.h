@@ -268,6 +268,59 @@ GF2X_API gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits
 GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b,
                            uint64_t *c, uint64_t count, void *stream);
 
+/* ------------------------------------------------------------------------
+ * The same method with m = 128 (Sec. 3 is written for general m; Sec. 4.3
+ * names GF(2^128) = GF(2)[x] / (x^128 + x^7 + x^2 + x + 1)).
+ *
+ * Sizes: n = max(128, next power of two >= nc); l = log2(n) - 7; n_p = 2^l =
+ * n/128 points; alpha = v_{l+64}, Sigma = alpha + V_l (Eq. 6 with m/2 = 64);
+ * Encode collapses l_m = 7 layers.  n <= 2^37, else GF2X_ETOOBIG.
+ *
+ * A vector of GF(2^128) elements is two uint64 words per element, low word
+ * (coefficients of x^0..x^63) first, so n_p points take n/64 words, the size
+ * of the n-bit array.  Element buffers must be 16-byte aligned.  The Cantor
+ * basis v_0..v_127 (Eq. 2) takes, at each step, the root with bit 0 clear.
+ * ---------------------------------------------------------------------- */
+
+/* Transform length n in bits for an na x nb product by the m = 128 method (0 if
+ * either length is 0). */
+GF2X_API uint64_t gf2x_m128_transform_bits(uint64_t na_bits, uint64_t nb_bits);
+
+/* Device workspace for gf2x_mul_m128: 3 n/8 bytes + 256 (0 if n > 2^37). */
+GF2X_API size_t gf2x_m128_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
+
+/* c = a * b in GF(2)[x] by Alg. 5 with m = 128: BasisCvt (Alg. 1, shared with
+ * m = 64), Encode into GF(2^128) elements, Butterfly on Sigma = v_{l+64} + V_l,
+ * pointwise GF(2^128) products, and back.  Same contract as gf2x_mul
+ * (arguments, layout of a, b, c, workspace alignment, no overlap of c with a,
+ * b or ws, graph replay of repeated calls).  The result equals gf2x_mul's
+ * bit for bit; a == b runs the transform too. */
+GF2X_API gf2x_status gf2x_mul_m128(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits,
+                          const uint64_t *b, uint64_t nb_bits, uint64_t *c,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Encode with m = 128: f_i = sum_{j<128} a_{j n_p + i} r_j (i < n_p), r_j =
+ * prod_{t<7} s_{l+t}(alpha)^{j_t} = prod_{t<7} v_{64-t}^{j_t}.  `novel`: n bits
+ * (8-byte aligned); f: n_p elements (16-byte aligned).  No overlap allowed. */
+GF2X_API gf2x_status gf2x_m128_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n_bits,
+                             uint64_t *f, void *stream);
+
+/* Decode with m = 128: the inverse of gf2x_m128_encode (n_p elements -> n bits). */
+GF2X_API gf2x_status gf2x_m128_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n_bits,
+                             uint64_t *novel, void *stream);
+
+/* Butterfly (Alg. 2) on n_p GF(2^128) elements at alpha = v_{l+64}, in place:
+ * output k is f(alpha + u_k), u_k the element with Cantor coordinates k. */
+GF2X_API gf2x_status gf2x_m128_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits, void *stream);
+
+/* The inverse of gf2x_m128_butterfly, in place. */
+GF2X_API gf2x_status gf2x_m128_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits, void *stream);
+
+/* Pointwise product in GF(2^128): c[i] = a[i] * b[i], i < count elements
+ * (2 count words each; 16-byte aligned).  c may alias a or b. */
+GF2X_API gf2x_status gf2x_m128_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b,
+                                uint64_t *c, uint64_t count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -118,6 +118,26 @@ def twiddle(l: int, i: int, s: int) -> int:
     return s_eval(i, sigma_point(l, s))
 
 
+class Twiddles:
+    """s_i(alpha + u_s) by linearity of s_i (Sec. 2.2.2): s_i(alpha) plus s_i(v_b) over the bits b of s."""
+
+    def __init__(self, l: int):
+        v = cantor_basis()
+        alpha = alpha_of(l)
+        self.s_alpha = [s_eval(i, alpha) for i in range(max(l, 1))]
+        self.s_v = [[s_eval(i, v[b]) for b in range(max(l, 1))] for i in range(max(l, 1))]
+
+    def __call__(self, i: int, s: int) -> int:
+        c = self.s_alpha[i]
+        b = 0
+        while s:
+            if s & 1:
+                c ^= self.s_v[i][b]
+            s >>= 1
+            b += 1
+        return c
+
+
 # ----------------------------------------------------------------- Encode
 def encode_multipliers(l: int) -> list[int]:
     """r_j = prod_t c_t^{j_t}, c_t = s_{l+t}(alpha) the multiplier of layer l + t, t < 7."""
@@ -179,10 +199,11 @@ def butterfly(g: list[int], l: int) -> list[int]:
     """Alg. 2 unrolled into layers l-1 .. 0: p0 += c p1, p1 += p0 with c = s_i(alpha + u_s)."""
     x = list(g)
     n_p = len(x)
+    tw = Twiddles(l)
     for i in range(l - 1, -1, -1):
         blk = 1 << (i + 1)
         for s in range(0, n_p, blk):
-            c = twiddle(l, i, s)
+            c = tw(i, s)
             for j in range(blk // 2):
                 x[s + j] ^= gf_mul(x[s + blk // 2 + j], c)
                 x[s + blk // 2 + j] ^= x[s + j]
@@ -193,10 +214,11 @@ def ibutterfly(y: list[int], l: int) -> list[int]:
     """Inverse of ``butterfly``: layers 0 .. l-1, p1 += p0 then p0 += c p1."""
     x = list(y)
     n_p = len(x)
+    tw = Twiddles(l)
     for i in range(l):
         blk = 1 << (i + 1)
         for s in range(0, n_p, blk):
-            c = twiddle(l, i, s)
+            c = tw(i, s)
             for j in range(blk // 2):
                 x[s + blk // 2 + j] ^= x[s + j]
                 x[s + j] ^= gf_mul(x[s + blk // 2 + j], c)

@@ -19,7 +19,8 @@ import os
 from .build import LIB as LIB_PATH
 
 __all__ = ["Context", "Gf2xError", "load_library", "transform_bits", "workspace_bytes",
-           "host_workspace_bytes", "product_bits", "ABI_FUNCTIONS", "STATUS"]
+           "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
+           "ABI_FUNCTIONS", "STATUS"]
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
           5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE"}
@@ -54,6 +55,14 @@ ABI_FUNCTIONS = {
     "gf2x_butterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_ibutterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
+    "gf2x_m128_transform_bits": (_U64, [_U64, _U64]),
+    "gf2x_m128_workspace_bytes": (_SZ, [_U64, _U64]),
+    "gf2x_mul_m128": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
+    "gf2x_m128_encode": (_ST, [_P, _P, _U64, _P, _P]),
+    "gf2x_m128_decode": (_ST, [_P, _P, _U64, _P, _P]),
+    "gf2x_m128_butterfly": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_m128_ibutterfly": (_ST, [_P, _P, _U64, _P]),
+    "gf2x_m128_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
     "gf2x_stage_count": (ctypes.c_int, []),
     "gf2x_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
     "gf2x_profile_enable": (_ST, [_P, ctypes.c_int]),
@@ -110,6 +119,14 @@ def workspace_bytes(na: int, nb: int) -> int:
 
 def host_workspace_bytes(na: int, nb: int) -> int:
     return int(load_library().gf2x_host_workspace_bytes(na, nb))
+
+
+def m128_transform_bits(na: int, nb: int) -> int:
+    return int(load_library().gf2x_m128_transform_bits(na, nb))
+
+
+def m128_workspace_bytes(na: int, nb: int) -> int:
+    return int(load_library().gf2x_m128_workspace_bytes(na, nb))
 
 
 def _words(nbits: int) -> int:
@@ -188,6 +205,23 @@ class Context:
                                   self._tensor_ptr(out, _words(nc), "out"),
                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                   self._stream(stream)), "gf2x_mul")
+        return out
+
+    def mul_m128(self, a, na: int, b, nb: int, out=None, workspace=None, stream=None):
+        """c = a * b by Alg. 5 with m = 128 (GF(2^128) points); same result as ``mul``."""
+        nc = product_bits(na, nb)
+        if out is None:
+            out = self.empty_words(_words(nc))
+        if nc == 0:
+            return out
+        need = m128_workspace_bytes(na, nb)
+        if workspace is None:
+            workspace = self.workspace(need)
+        _check(self._lib.gf2x_mul_m128(self._h, self._tensor_ptr(a, _words(na), "a"), na,
+                                       self._tensor_ptr(b, _words(nb), "b"), nb,
+                                       self._tensor_ptr(out, _words(nc), "out"),
+                                       ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                       self._stream(stream)), "gf2x_mul_m128")
         return out
 
     def forward_transform(self, b, nb: int, n: int, out=None, workspace=None, stream=None):
@@ -323,4 +357,41 @@ class Context:
         _check(self._lib.gf2x_pointwise(self._h, self._tensor_ptr(a, count, "a"), self._tensor_ptr(b, count, "b"),
                                         self._tensor_ptr(out, count, "out"), count, self._stream(stream)),
                "gf2x_pointwise")
+        return out
+
+    # ------------------------------------------------------ stages, m = 128
+    # Element vectors hold two words per GF(2^128) point (low word first).
+    def m128_encode(self, novel, n: int, out=None, stream=None):
+        if out is None:
+            out = self.empty_words(n // 64)
+        _check(self._lib.gf2x_m128_encode(self._h, self._tensor_ptr(novel, n // 64, "novel"), n,
+                                          self._tensor_ptr(out, n // 64, "out"), self._stream(stream)),
+               "gf2x_m128_encode")
+        return out
+
+    def m128_decode(self, h, n: int, out=None, stream=None):
+        if out is None:
+            out = self.empty_words(n // 64)
+        _check(self._lib.gf2x_m128_decode(self._h, self._tensor_ptr(h, n // 64, "h"), n,
+                                          self._tensor_ptr(out, n // 64, "out"), self._stream(stream)),
+               "gf2x_m128_decode")
+        return out
+
+    def m128_butterfly(self, f, n: int, stream=None, inverse: bool = False):
+        fn = self._lib.gf2x_m128_ibutterfly if inverse else self._lib.gf2x_m128_butterfly
+        _check(fn(self._h, self._tensor_ptr(f, n // 64, "f"), n, self._stream(stream)),
+               "gf2x_m128_ibutterfly" if inverse else "gf2x_m128_butterfly")
+        return f
+
+    def m128_ibutterfly(self, f, n: int, stream=None):
+        return self.m128_butterfly(f, n, stream, inverse=True)
+
+    def m128_pointwise(self, a, b, out=None, stream=None):
+        count = a.numel() // 2
+        if out is None:
+            out = self.empty_words(2 * count)
+        _check(self._lib.gf2x_m128_pointwise(self._h, self._tensor_ptr(a, 2 * count, "a"),
+                                             self._tensor_ptr(b, 2 * count, "b"),
+                                             self._tensor_ptr(out, 2 * count, "out"), count, self._stream(stream)),
+               "gf2x_m128_pointwise")
         return out

@@ -147,6 +147,7 @@ int log2_u64(u64 x)
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 bool overlap(const void *p, size_t pb, const void *q, size_t qb)
 {
@@ -256,7 +257,8 @@ struct StageScope {
 enum OpKind {
     OP_MUL = 0,               // c = a * b
     OP_MUL_TRANSFORMED = 1,   // c = a * b, b given as its transform at b's pointer
-    OP_FORWARD_TRANSFORM = 2  // c = transform of a (na bits) at length nb
+    OP_FORWARD_TRANSFORM = 2, // c = transform of a (na bits) at length nb
+    OP_MUL128 = 3             // c = a * b by the m = 128 method
 };
 
 struct GraphEntry {
@@ -452,11 +454,57 @@ gf2x_status mul_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb
     return run_class(ctx, r, st);
 }
 
+// ---------------------------------------------------------------- m = 128
+// The same method with GF(2^128) points (Sec. 3 for general m, Sec. 4.3):
+// n = max(128, next_pow2(nc)), l = log2(n) - 7, n_p = 2^l points of two words,
+// so X, Y, T have the m = 64 sizes.  BasisCvt, load and store are shared.
+u64 transform_bits128(u64 na, u64 nb)
+{
+    u64 nc = product_bits(na, nb);
+    if (!nc) return 0;
+    u64 n = next_pow2(nc);
+    return n < 128 ? 128 : n;
+}
+
+gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                          cudaStream_t st)
+{
+    const u64 n = transform_bits128(na, nb);
+    const int l = log2_u64(n) - 7;
+    const u64 La = next_pow2(na) < 64 ? 64 : next_pow2(na);
+    const u64 Lb = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
+    const size_t buf = buffer_bytes(n);
+    u64 *X = (u64 *)ws, *Y = (u64 *)((char *)ws + buf), *T = (u64 *)((char *)ws + 2 * buf);
+    if (La == Lb && 2 * La <= n) {
+        // both operands in one launch per stage: a in the lower half of T, b in the upper
+        const u64 half = n / 128;
+        { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_pair(ctx, a, na, b, nb, T, half, half, st)); }
+        { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, La, false, 2, half, X, st)); }
+        { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, X, La, 2, half, (u64)(Y - X), st)); }
+    } else {
+        for (int which = 0; which < 2; ++which) {
+            u64 *F = which ? Y : X;
+            const u64 L = which ? Lb : La;
+            { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, which ? b : a, which ? nb : na, T, n / 64, st)); }
+            { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, F, st)); }
+            { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, F, L, 1, 0, 0, st)); }
+        }
+    }
+    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::m128_butterfly_top_pair(ctx, X, Y, l, 1, 0, st)); }
+    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::m128_butterfly_bottom_fused(ctx, X, Y, l, 1, 0, st)); }
+    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::m128_butterfly_top_inverse(ctx, X, l, 1, 0, st)); }
+    { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::m128_decode(ctx, X, l, T, 1, 0, st)); }
+    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st)); }
+    { StageScope g(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, product_bits(na, nb), c, st)); }
+    return GF2X_OK;
+}
+
 gf2x_status op_device(gf2x_ctx *ctx, int kind, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
                       cudaStream_t st)
 {
     if (kind == OP_MUL_TRANSFORMED) return mul_transformed_device(ctx, a, na, b, nb, c, ws, st);
     if (kind == OP_FORWARD_TRANSFORM) return forward_transform_device(ctx, a, na, nb, c, ws, st);
+    if (kind == OP_MUL128) return mul128_device(ctx, a, na, b, nb, c, ws, st);
     return mul_device(ctx, a, na, b, nb, c, ws, st);
 }
 
@@ -654,6 +702,7 @@ struct BatchCache {
 constexpr size_t kMaxBatchGraphs = 8;
 
 bool valid_n(u64 n) { return n >= 64 && n <= kMaxTransformBits && (n & (n - 1)) == 0; }
+bool valid_n128(u64 n) { return n >= 128 && valid_n(n); }
 
 }  // namespace
 
@@ -742,9 +791,27 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     ctx->d_enc = ctx->d_tables + 2048;
     ctx->d_dec = ctx->d_tables + 4096;
     ctx->d_cantor = ctx->d_tables + 6144;
+    std::vector<u64> host128(gf2x::kTables128Words);
+    if (!gf2x::m128_build_tables(host128.data())) {
+        cudaFree(ctx->d_tables);
+        cudaFree(ctx->d_status);
+        return fail(GF2X_EINVAL);
+    }
+    if (cudaMalloc(&ctx->d_tables128, host128.size() * sizeof(u64)) != cudaSuccess) {
+        cudaFree(ctx->d_tables);
+        cudaFree(ctx->d_status);
+        return fail(GF2X_ENOMEM);
+    }
+    ctx->d_cvt128 = ctx->d_tables128;
+    ctx->d_enc128 = ctx->d_tables128 + 4096;
+    ctx->d_dec128 = ctx->d_tables128 + 4096 + 8192;
+    ctx->d_cantor128 = ctx->d_tables128 + 4096 + 2 * 8192;
     if (cudaMemcpy(ctx->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_tables128, host128.data(), host128.size() * sizeof(u64), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
         cudaMemset(ctx->d_status, 0, kAlign) != cudaSuccess) {
         cudaFree(ctx->d_tables);
+        cudaFree(ctx->d_tables128);
         cudaFree(ctx->d_status);
         return fail(GF2X_ECUDA);
     }
@@ -776,6 +843,7 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx)
     }
     gf2x::tuner_destroy(ctx->tuner);
     cudaFree(ctx->d_tables);
+    cudaFree(ctx->d_tables128);
     cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -992,6 +1060,88 @@ gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, 
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_POINTWISE, (cudaStream_t)stream);
     return from_cuda(gf2x::pointwise(ctx, a, b, c, count, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------ m = 128
+uint64_t gf2x_m128_transform_bits(uint64_t na, uint64_t nb) { return transform_bits128(na, nb); }
+
+size_t gf2x_m128_workspace_bytes(uint64_t na, uint64_t nb)
+{
+    u64 n = transform_bits128(na, nb);
+    if (!n || n > kMaxTransformBits) return 0;
+    return 3 * buffer_bytes(n) + kAlign;
+}
+
+gf2x_status gf2x_mul_m128(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *c,
+                          void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    const u64 nc = product_bits(na, nb);
+    if (!nc) return GF2X_OK;
+    const u64 n = transform_bits128(na, nb);
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!a || !b || !c || !ws || !aligned8(a) || !aligned8(b) || !aligned8(c) || ((uintptr_t)ws % kAlign))
+        return GF2X_EINVAL;
+    const size_t need = gf2x_m128_workspace_bytes(na, nb);
+    if (ws_bytes < need) return GF2X_ENOSPACE;
+    const size_t cb = (size_t)((nc + 63) / 64) * 8;
+    if (overlap(c, cb, a, (size_t)((na + 63) / 64) * 8) || overlap(c, cb, b, (size_t)((nb + 63) / 64) * 8) ||
+        overlap(c, cb, ws, need))
+        return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    return op_graph(ctx, OP_MUL128, a, na, b, nb, c, ws, (cudaStream_t)stream);
+}
+
+gf2x_status gf2x_m128_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64_t *f, void *stream)
+{
+    if (!ctx || !novel || !f || !aligned8(novel) || !aligned16(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n128(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
+    return from_cuda(gf2x::m128_encode(ctx, novel, log2_u64(n) - 7, f, n, 1, 0, 0, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_m128_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)
+{
+    if (!ctx || !novel || !h || !aligned8(novel) || !aligned16(h)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n128(n) || overlap(novel, n / 8, h, n / 8)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_DECODE, (cudaStream_t)stream);
+    return from_cuda(gf2x::m128_decode(ctx, h, log2_u64(n) - 7, novel, 1, 0, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_m128_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
+{
+    if (!ctx || !f || !aligned16(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n128(n)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_BUTTERFLY, (cudaStream_t)stream);
+    return from_cuda(gf2x::m128_butterfly(ctx, f, log2_u64(n) - 7, false, 1, 0, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_m128_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
+{
+    if (!ctx || !f || !aligned16(f)) return GF2X_EINVAL;
+    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (!valid_n128(n)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_IBUTTERFLY, (cudaStream_t)stream);
+    return from_cuda(gf2x::m128_butterfly(ctx, f, log2_u64(n) - 7, true, 1, 0, (cudaStream_t)stream));
+}
+
+gf2x_status gf2x_m128_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *c, uint64_t count,
+                                void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    if (!count) return GF2X_OK;
+    if (!a || !b || !c || !aligned16(a) || !aligned16(b) || !aligned16(c)) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    StageScope sc(ctx, STAGE_POINTWISE, (cudaStream_t)stream);
+    return from_cuda(gf2x::m128_pointwise(ctx, a, b, c, count, (cudaStream_t)stream));
 }
 
 gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream)

@@ -31,34 +31,6 @@ __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_
 // (Sec. 4.4's block-swap transpose: a 32-bit half swap in registers, then
 // five exchange rounds across lanes) and applies R through 8-bit window tables
 // loaded once per block.  Rows at or above `rows` are zero and are not read.
-constexpr u64 kM16 = 0x0000FFFF0000FFFFull, kM8 = 0x00FF00FF00FF00FFull, kM4 = 0x0F0F0F0F0F0F0F0Full,
-              kM2 = 0x3333333333333333ull, kM1 = 0x5555555555555555ull;
-
-// Lane t holds rows t (A) and t + 32 (B) of a 64x64 bit matrix (bit c of row
-// r = M[r][c]); on return A = column t and B = column t + 32 (bit r = M[r][c]).
-// Applied to columns it returns rows.
-__device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
-{
-    const u64 a2 = (A & 0x00000000FFFFFFFFull) | (B << 32);
-    const u64 b2 = (A >> 32) | (B & 0xFFFFFFFF00000000ull);
-    A = a2;
-    B = b2;
-    const u64 masks[5] = {kM16, kM8, kM4, kM2, kM1};
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int j = 16 >> s;
-        const u64 m = masks[s];
-        const u64 ya = __shfl_xor_sync(0xffffffffu, A, j), yb = __shfl_xor_sync(0xffffffffu, B, j);
-        if (lane & j) {
-            A = ((ya & ~m) >> j) | (A & ~m);
-            B = ((yb & ~m) >> j) | (B & ~m);
-        } else {
-            A = (A & m) | ((ya & m) << j);
-            B = (B & m) | ((yb & m) << j);
-        }
-    }
-}
-
 constexpr int kPad = kCols + 1;      // padded row of the staging tile
 
 __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, int rows,

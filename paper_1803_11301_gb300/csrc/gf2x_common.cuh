@@ -66,6 +66,36 @@ __device__ __forceinline__ u64 lin64(const u64 *__restrict__ t, u64 x)
     return r;
 }
 
+// 64x64 bit transpose across a warp (Sec. 4.4's block-swap transpose: a
+// 32-bit half swap in registers, then five exchange rounds across lanes).
+constexpr u64 kM16 = 0x0000FFFF0000FFFFull, kM8 = 0x00FF00FF00FF00FFull, kM4 = 0x0F0F0F0F0F0F0F0Full,
+              kM2 = 0x3333333333333333ull, kM1 = 0x5555555555555555ull;
+
+// Lane t holds rows t (A) and t + 32 (B) of a 64x64 bit matrix (bit c of row
+// r = M[r][c]); on return A = column t and B = column t + 32 (bit r = M[r][c]).
+// Applied to columns it returns rows.
+__device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
+{
+    const u64 a2 = (A & 0x00000000FFFFFFFFull) | (B << 32);
+    const u64 b2 = (A >> 32) | (B & 0xFFFFFFFF00000000ull);
+    A = a2;
+    B = b2;
+    const u64 masks[5] = {kM16, kM8, kM4, kM2, kM1};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const u64 m = masks[s];
+        const u64 ya = __shfl_xor_sync(0xffffffffu, A, j), yb = __shfl_xor_sync(0xffffffffu, B, j);
+        if (lane & j) {
+            A = ((ya & ~m) >> j) | (A & ~m);
+            B = ((yb & ~m) >> j) | (B & ~m);
+        } else {
+            A = (A & m) | ((ya & m) << j);
+            B = (B & m) | ((yb & m) << j);
+        }
+    }
+}
+
 // One product of a batch as the device sees it (the job table lives in the
 // workspace).  nc = na + nb - 1 bits (0 if either is 0).
 struct JobDev {
@@ -106,6 +136,12 @@ struct gf2x_ctx {
     int *d_status;      // device status word (gf2x_status)
     GridSync *d_sync;   // barrier state for the stage entry points
     u64 cantor[64];     // host copy of the Cantor basis
+    // GF(2^128) variant (m128.cu): 128-bit entries as (lo, hi) word pairs
+    u64 *d_tables128;   // one allocation holding the tables below
+    u64 *d_cvt128;      // 8 x 256: Cantor coordinates < 2^64 -> polynomial form
+    u64 *d_enc128;      // 16 x 256: the 128 bits (a_{j n_p + i})_j -> f_i  (matrix R)
+    u64 *d_dec128;      // 16 x 256: f_i -> bits                             (matrix R^{-1})
+    u64 *d_cantor128;   // v_0 .. v_127
 
     // launch accounting and optional per-stage event timing (host side)
     int stage;                          // stage the next launches belong to
@@ -174,5 +210,23 @@ cudaError_t load_pair(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb,
 cudaError_t store_bits(gf2x_ctx *ctx, const u64 *src, u64 nbits, u64 *dst, cudaStream_t st);
 // c = a^2 (2 na - 1 bits) by spreading the bits of a: no transform.
 cudaError_t square_bits(gf2x_ctx *ctx, const u64 *a, u64 na, u64 *c, cudaStream_t st);
+
+
+// ---- the GF(2^128) variant (m128.cu).  A point is two words (lo, hi); a
+// transform of n bits holds n_p = n/128 points in n/64 words.
+// Number of u64 words of the tables and filling them (host side); false if a
+// step of the set-up fails (a singular system).
+constexpr size_t kTables128Words = 2 * (8 * 256 + 16 * 256 + 16 * 256 + 128);
+bool m128_build_tables(u64 *host);
+// l = log2(n_p) = log2(n) - 7.
+cudaError_t m128_encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
+                        u64 out_stride, cudaStream_t st);
+cudaError_t m128_decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st);
+cudaError_t m128_butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st);
+cudaError_t m128_butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t m128_butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int count, u64 stride,
+                                        cudaStream_t st);
+cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
+cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
 
 }  // namespace gf2x

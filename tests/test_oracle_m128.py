@@ -172,3 +172,11 @@ def test_transform_length_rule():
     assert G.transform_length(64, 65) == 128
     assert G.transform_length(65, 65) == 256
     assert G.transform_length(1 << 30, 1 << 30) == 1 << 31
+
+
+def test_twiddles_by_linearity_equal_the_definition():
+    for l in [1, 3, 6]:
+        tw = G.Twiddles(l)
+        for i in range(l):
+            for s in range(0, 1 << l, 1 << (i + 1)):
+                assert tw(i, s) == G.twiddle(l, i, s)
