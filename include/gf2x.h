@@ -274,7 +274,9 @@ GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint
  *
  * Sizes: n = max(128, next power of two >= nc); l = log2(n) - 7; n_p = 2^l =
  * n/128 points; alpha = v_{l+64}, Sigma = alpha + V_l (Eq. 6 with m/2 = 64);
- * Encode collapses l_m = 7 layers.  n <= 2^37, else GF2X_ETOOBIG.
+ * Encode collapses l_m = 7 layers.  n <= 2^38, else GF2X_ETOOBIG: the
+ * Sec. 3.1 limit with m = 128, (m/2) 2^(m/2) = 2^70 bits, does not bind; one
+ * GB300's memory does (a 2^37 x 2^37-bit product holds 160 GB).
  *
  * A vector of GF(2^128) elements is two uint64 words per element, low word
  * (coefficients of x^0..x^63) first, so n_p points take n/64 words, the size
@@ -286,7 +288,7 @@ GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint
  * either length is 0). */
 GF2X_API uint64_t gf2x_m128_transform_bits(uint64_t na_bits, uint64_t nb_bits);
 
-/* Device workspace for gf2x_mul_m128: 3 n/8 bytes + 256 (0 if n > 2^37). */
+/* Device workspace for gf2x_mul_m128: 3 n/8 bytes + 256 (0 if n > 2^38). */
 GF2X_API size_t gf2x_m128_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
 
 /* c = a * b in GF(2)[x] by Alg. 5 with m = 128: BasisCvt (Alg. 1, shared with

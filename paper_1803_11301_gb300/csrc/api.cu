@@ -23,6 +23,10 @@
 namespace {
 
 constexpr u64 kMaxTransformBits = 1ull << 37;    // Sec. 3.1 length limit, m = 64
+// m = 128: the Sec. 3.1 limit is 2^70 bits; the cap is one GB300's memory:
+// a product at n = 2^38 holds 3 n/8 bytes of workspace plus n/2 of operands
+// and result, 160 GB of the 288 GB (n = 2^39 would need 320 GB).
+constexpr u64 kMaxTransformBits128 = 1ull << 38;
 constexpr size_t kAlign = 256;
 
 // ------------------------------------------------------------ host GF(2^64)
@@ -702,7 +706,7 @@ struct BatchCache {
 constexpr size_t kMaxBatchGraphs = 8;
 
 bool valid_n(u64 n) { return n >= 64 && n <= kMaxTransformBits && (n & (n - 1)) == 0; }
-bool valid_n128(u64 n) { return n >= 128 && valid_n(n); }
+bool valid_n128(u64 n) { return n >= 128 && n <= kMaxTransformBits128 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
@@ -1068,7 +1072,7 @@ uint64_t gf2x_m128_transform_bits(uint64_t na, uint64_t nb) { return transform_b
 size_t gf2x_m128_workspace_bytes(uint64_t na, uint64_t nb)
 {
     u64 n = transform_bits128(na, nb);
-    if (!n || n > kMaxTransformBits) return 0;
+    if (!n || n > kMaxTransformBits128) return 0;
     return 3 * buffer_bytes(n) + kAlign;
 }
 
@@ -1079,7 +1083,7 @@ gf2x_status gf2x_mul_m128(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const u
     const u64 nc = product_bits(na, nb);
     if (!nc) return GF2X_OK;
     const u64 n = transform_bits128(na, nb);
-    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (n > kMaxTransformBits128) return GF2X_ETOOBIG;
     if (!a || !b || !c || !ws || !aligned8(a) || !aligned8(b) || !aligned8(c) || ((uintptr_t)ws % kAlign))
         return GF2X_EINVAL;
     const size_t need = gf2x_m128_workspace_bytes(na, nb);
@@ -1096,7 +1100,7 @@ gf2x_status gf2x_mul_m128(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const u
 gf2x_status gf2x_m128_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, uint64_t *f, void *stream)
 {
     if (!ctx || !novel || !f || !aligned8(novel) || !aligned16(f)) return GF2X_EINVAL;
-    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (n > kMaxTransformBits128) return GF2X_ETOOBIG;
     if (!valid_n128(n) || overlap(novel, n / 8, f, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_ENCODE, (cudaStream_t)stream);
@@ -1106,7 +1110,7 @@ gf2x_status gf2x_m128_encode(gf2x_ctx *ctx, const uint64_t *novel, uint64_t n, u
 gf2x_status gf2x_m128_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint64_t *novel, void *stream)
 {
     if (!ctx || !novel || !h || !aligned8(novel) || !aligned16(h)) return GF2X_EINVAL;
-    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (n > kMaxTransformBits128) return GF2X_ETOOBIG;
     if (!valid_n128(n) || overlap(novel, n / 8, h, n / 8)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_DECODE, (cudaStream_t)stream);
@@ -1116,7 +1120,7 @@ gf2x_status gf2x_m128_decode(gf2x_ctx *ctx, const uint64_t *h, uint64_t n, uint6
 gf2x_status gf2x_m128_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
 {
     if (!ctx || !f || !aligned16(f)) return GF2X_EINVAL;
-    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (n > kMaxTransformBits128) return GF2X_ETOOBIG;
     if (!valid_n128(n)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_BUTTERFLY, (cudaStream_t)stream);
@@ -1126,7 +1130,7 @@ gf2x_status gf2x_m128_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *st
 gf2x_status gf2x_m128_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n, void *stream)
 {
     if (!ctx || !f || !aligned16(f)) return GF2X_EINVAL;
-    if (n > kMaxTransformBits) return GF2X_ETOOBIG;
+    if (n > kMaxTransformBits128) return GF2X_ETOOBIG;
     if (!valid_n128(n)) return GF2X_EINVAL;
     DeviceGuard g(ctx->device);
     StageScope sc(ctx, STAGE_IBUTTERFLY, (cudaStream_t)stream);

@@ -24,13 +24,27 @@
 namespace gf2x {
 namespace {
 
+// Launch-shape constants; each can be overridden at compile time (-D) to
+// measure alternatives.
+#ifndef GF2X_M128_BOTTOM
+#define GF2X_M128_BOTTOM 10
+#endif
+#ifndef GF2X_M128_TABLE_MIN
+#define GF2X_M128_TABLE_MIN 4
+#endif
+#ifndef GF2X_M128_TOP
+#define GF2X_M128_TOP 3
+#endif
+#ifndef GF2X_M128_CHUNK
+#define GF2X_M128_CHUNK 4
+#endif
 constexpr u64 kMod128Low = 0x87;      // x^7 + x^2 + x + 1
-constexpr int kBottom128 = 10;        // bottom tile: 2^10 points (16 KiB per transform)
-constexpr int kTableMin128 = 4;       // bottom layers >= 4 multiply through tables
-constexpr int kTopLayers128 = 3;      // layers per top pass
+constexpr int kBottom128 = GF2X_M128_BOTTOM;       // bottom tile: 2^10 points (16 KiB per transform)
+constexpr int kTableMin128 = GF2X_M128_TABLE_MIN;  // bottom layers >= 4 multiply through tables
+constexpr int kTopLayers128 = GF2X_M128_TOP;       // layers per top pass (<= 4)
 constexpr int kThreads128 = 256;
 constexpr int kTab128 = 1024;         // u64 words per multiplication table (8 KiB)
-constexpr int kChunk128 = 8;          // tables built at a time in the bottom tile
+constexpr int kChunk128 = GF2X_M128_CHUNK;         // tables built at a time in the bottom tile
 constexpr int kCols128 = 16;          // word columns per Encode/Decode block
 constexpr int kPad128 = kCols128 + 1;
 constexpr int kLinWords = 16 * 256 * 2;  // words of a 128-bit byte-window table

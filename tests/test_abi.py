@@ -69,3 +69,16 @@ def test_no_device_path_reports_enodev(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.gf2x_ctx_create(ctypes.byref(h), 0) == 6                      # ENODEV, no fallback
+
+
+def test_m128_size_rules_match_the_oracle(lib):
+    from paper_1803_11301_gb300 import m128_transform_bits, m128_workspace_bytes
+    from oracle import m128 as G
+    for na, nb in [(1, 1), (64, 65), (65, 65), (1 << 16, 1 << 16), (5, 1 << 20), (1 << 30, 1 << 30),
+                   (1 << 37, 1 << 37)]:
+        n = G.transform_length(na, nb)
+        assert m128_transform_bits(na, nb) == n
+        assert m128_workspace_bytes(na, nb) == 3 * ((n // 8 + 255) // 256 * 256) + 256
+    assert m128_transform_bits(0, 5) == 0 and m128_workspace_bytes(7, 0) == 0
+    assert m128_workspace_bytes(1 << 37, (1 << 37) + 2) == 0       # n = 2^39 > 2^38
+    assert lib.gf2x_mul_m128(None, None, 1, None, 1, None, None, 0, None) == 1      # EINVAL

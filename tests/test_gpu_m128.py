@@ -160,6 +160,17 @@ def test_product_2e30_modular(ctx):
     assert O.words_to_int(c[-1:]) >> ((na + nb - 1) % 64) == 0
 
 
+def test_product_2e32_generic_basis_cvt_modular(ctx):
+    # n = 2^33 (K = 33, BasisCvt by the generic step kernels), 16 modular checks
+    na = nb = 1 << 32
+    a = synth.operand(synth.config_seed(14, 200), na)
+    b = synth.operand(synth.config_seed(14, 201), nb)
+    c = host(ctx.mul_m128(dev(a), na, dev(b), nb))
+    lows = O.random_irreducibles(synth.config_seed(14, 97), 16)
+    assert O.modcheck(a, na, b, nb, c, na + nb - 1, lows).all()
+    assert O.words_to_int(c[-1:]) >> ((na + nb - 1) % 64) == 0
+
+
 def test_same_product_as_m64_path(ctx):
     for na, nb in [(1 << 18, 1 << 18), (300001, 77777)]:
         a = dev(synth.operand(synth.config_seed(15, na), na))

@@ -207,6 +207,18 @@ def test_length_sweep_modular(ctx):
         assert O.modcheck(a, na, b, nb, c, na + nb - 1, lows).all(), e
 
 
+def test_product_beyond_structured_basis_cvt(ctx):
+    # n = 2^33: BasisCvt at K = 33 runs the generic step kernels (the structured
+    # ones cover K <= 32); 2^32 x 2^32 bits, 16 modular checks and the zero tail
+    na = nb = 1 << 32
+    a = synth.operand(synth.config_seed(3, 200), na)
+    b = synth.operand(synth.config_seed(3, 201), nb)
+    c = host(ctx.mul(dev(a), na, dev(b), nb))
+    lows = O.random_irreducibles(synth.config_seed(3, 97), 16)
+    assert O.modcheck(a, na, b, nb, c, na + nb - 1, lows).all()
+    assert O.words_to_int(c[-1:]) >> ((na + nb - 1) % 64) == 0
+
+
 def test_host_entry_point(ctx):
     for na, nb in [(1, 1), (1000, 77), (1 << 18, 1 << 17)]:
         a = synth.operand(5 + na, na)
