@@ -70,19 +70,23 @@ NUM_SMS = 152
 # table in shared memory, 16 x 8 B = 128 B per product) is bound by the
 # shared-memory port, 128 B per SM-clock: at most 1 product per SM per clock.
 PRODUCTS_PER_SM_CLOCK = 1.0
-BOTTOM_LAYERS = 11            # low layers done by the fused bottom kernel
+BOTTOM_LAYERS = 11            # default low layers of the fused bottom kernel (the library reports its choice)
 # GF(2^128) points: the table product reads 32 windows x 16 B = 512 B of
-# shared memory, so at most 1/4 product per SM per clock; 10 bottom layers.
+# shared memory, so at most 1/4 product per SM per clock; up to 10 bottom layers.
 PRODUCTS_PER_SM_CLOCK_128 = 0.25
 BOTTOM_LAYERS_128 = 10
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a stage's
-# kernel, keyed by (stage, na, nb), from one capture of the same workload
-# (profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md gives both captures).
+# kernel, keyed by (stage, na, nb, field bits, bottom layers), from one capture of the same workload
+# (profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md, profiles/k128_bfly_bottom_gf2x_mul_m128_2e30x2e30.md,
+# profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/launch_list_gf2x_mul_m128_2e24x2e24.md).
 # An entry is removed when its kernel changes; a missing entry reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {
-    ("bottom_fused", 1 << 24, 1 << 24, 64): 8426240 + 0,
-    ("bottom_fused", 1 << 30, 1 << 30, 64): 536919552 + 224388864,
+TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers)
+    ("bottom_fused", 1 << 24, 1 << 24, 64, 11): 8426240 + 0,
+    ("bottom_fused", 1 << 24, 1 << 24, 64, 9): 8426240 + 0,
+    ("bottom_fused", 1 << 24, 1 << 24, 128, 9): 8467968 + 0,
+    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): 536919552 + 224388864,
+    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): 537235968 + 225500928,
 }
 
 
@@ -204,6 +208,17 @@ def scaled_oracle_workload(na, nb):
     return na, nb
 
 
+def single_config(args):
+    """The configuration of a single-product run, with --log2-bits applied."""
+    cfg = dict(CONFIGS[args.config])
+    if args.log2_bits is not None and "na" in cfg:
+        k = args.log2_bits
+        cfg["na"] = cfg["nb"] = 1 << k
+        cfg["name"] = f"single product 2^{k} x 2^{k} bits, uniform random" + (
+            ", GF(2^128) points (gf2x_mul_m128)" if cfg.get("field") == 128 else "")
+    return cfg
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -213,7 +228,7 @@ def run_reference(args, world, rank):
         print(json.dumps({"impl": "reference", "unavailable": "the serving mix has 2^28-bit operands, minutes per "
                           "product for the CPU oracle; the reference arm covers configs 1-4 and 6"}), flush=True)
         return
-    cfg = CONFIGS[args.config]
+    cfg = single_config(args)
     na, nb = scaled_oracle_workload(cfg["na"], cfg["nb"])
     from oracle import clmul as O
     O.build()
@@ -273,13 +288,17 @@ def run_reference_batch(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def stage_work(stage, na, nb, n, products, field=64):
+def stage_work(stage, na, nb, n, products, field=64, bottom_layers=None):
     """Algorithmic work of one stage over `products` products: (amount, kind).
 
-    kind "mul": GF(2^m) products (one per butterfly); kind "hbm": bytes."""
+    kind "mul": GF(2^m) products (one per butterfly); kind "hbm": bytes.
+    bottom_layers: Butterfly layers done by the fused low-layer kernel (the
+    library's choice, gf2x_bottom_layers); the rest are top passes."""
     l = n.bit_length() - 1 - (7 if field == 128 else 6)
     n_p = 1 << l
-    bt = min(BOTTOM_LAYERS_128 if field == 128 else BOTTOM_LAYERS, l)
+    if bottom_layers is None:
+        bottom_layers = BOTTOM_LAYERS_128 if field == 128 else BOTTOM_LAYERS
+    bt = min(bottom_layers, l)
     fw = 2                         # two forward transforms
     la = max(64, 1 << max(0, (na - 1).bit_length()))
     lb = max(64, 1 << max(0, (nb - 1).bit_length()))
@@ -313,7 +332,7 @@ def run_gpu(args, world, rank, local):
     lib_build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg = CONFIGS[args.config]
+    cfg = single_config(args)
     na, nb = cfg["na"], cfg["nb"]
     field = cfg.get("field", 64)
     nc = na + nb - 1
@@ -352,6 +371,8 @@ def run_gpu(args, world, rank, local):
         dist_barrier(world)
         torch.cuda.synchronize(dev)
         prof = None
+        if not profiled:
+            torch.cuda.profiler.start()          # `ncu --profile-from-start off` sees this region only
         for k in range(args.steps):
             flush.fill_(k)
             starts[k].record(stream)
@@ -360,6 +381,8 @@ def run_gpu(args, world, rank, local):
             if profiled:
                 prof = ctx.profile_read()        # waits for this step; outside the events
         torch.cuda.synchronize(dev)
+        if not profiled:
+            torch.cuda.profiler.stop()
         dist_barrier(world)
         if profiled:
             prof = ctx.profile_read()
@@ -417,9 +440,10 @@ def run_gpu(args, world, rank, local):
     # roofline of the dominant stage
     hbm_peak, sm_max_mhz, peak_src = load_peaks()
     n = 1 << max(7 if field == 128 else 6, (nc - 1).bit_length())
+    bottom_layers = ctx.bottom_layers(na, nb, field)
     stages = {}
     for name, (ms, nl) in prof.items():
-        work, kind = stage_work(name, na, nb, n, args.steps, field)
+        work, kind = stage_work(name, na, nb, n, args.steps, field, bottom_layers)
         stages[name] = {"ms": ms / args.steps, "launches_per_step": nl / args.steps, "bound": kind,
                         "work_per_step": work / args.steps}
     dom = max(stages, key=lambda k: stages[k]["ms"])
@@ -431,12 +455,12 @@ def run_gpu(args, world, rank, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s", "frac": achieved / peak,
                 "peak_source": (f"derived: {NUM_SMS} SMs x {sm_max_mhz:.0f} MHz x {per_clock:g} GF(2^{field}) "
                                 "product per SM-clock (shared-memory port bound of the table product)"),
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field)), "kernel_stage": dom,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field, bottom_layers)), "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
     else:
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field)),
+                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field, bottom_layers)),
                 "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
 
@@ -446,6 +470,7 @@ def run_gpu(args, world, rank, local):
             "ms_per_step": ms_per_step, "us_per_product": 1e3 * ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": cfg["name"], "na_bits": na, "nb_bits": nb, "transform_bits": n, "field_bits": field,
+                       "bottom_layers": bottom_layers,
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"{world} independent replica(s)"},
             "hbm_compulsory": {"bytes_per_product": compulsory,
@@ -793,6 +818,8 @@ def main():
                     choices=["butterfly", "ibutterfly", "basis_cvt", "ibasis_cvt", "encode", "decode", "pointwise"],
                     help="time one stage alone through its entry point (profiling aid)")
     ap.add_argument("--log2-points", type=int, default=24, help="n_p = 2^this GF(2^64) points for --stage")
+    ap.add_argument("--log2-bits", type=int, default=None,
+                    help="operands of 2^this bits for the single-product configs (1-3, 7, 8): the length sweep")
     args = ap.parse_args()
     if args.stage:
         run_stage(args)

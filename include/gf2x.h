@@ -208,6 +208,13 @@ GF2X_API gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream);
  * traps. */
 GF2X_API gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream);
 
+/* Butterfly layers (Alg. 2) that gf2x_mul runs in its fused low-layer kernel
+ * for an na x nb product, the rest running as passes over HBM: the depth the
+ * context's tuner measured at the first product of this transform length, or
+ * the default before that.  -1 for a NULL context or an empty or too long
+ * product.  Informational (profiling and roofline accounting). */
+GF2X_API int gf2x_bottom_layers(gf2x_ctx *ctx, uint64_t na_bits, uint64_t nb_bits);
+
 /* ------------------------------------------------------------------------
  * Per-stage profiling.  Stage k (0 <= k < gf2x_stage_count()) is one step of
  * Alg. 5 as named by gf2x_stage_name(k): load, basis_cvt, encode, butterfly,
@@ -287,6 +294,9 @@ GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint
 /* Transform length n in bits for an na x nb product by the m = 128 method (0 if
  * either length is 0). */
 GF2X_API uint64_t gf2x_m128_transform_bits(uint64_t na_bits, uint64_t nb_bits);
+
+/* As gf2x_bottom_layers, for gf2x_mul_m128. */
+GF2X_API int gf2x_m128_bottom_layers(gf2x_ctx *ctx, uint64_t na_bits, uint64_t nb_bits);
 
 /* Device workspace for gf2x_mul_m128: 3 n/8 bytes + 256 (0 if n > 2^38). */
 GF2X_API size_t gf2x_m128_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);

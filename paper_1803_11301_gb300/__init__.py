@@ -55,7 +55,9 @@ ABI_FUNCTIONS = {
     "gf2x_butterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_ibutterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
+    "gf2x_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
     "gf2x_m128_transform_bits": (_U64, [_U64, _U64]),
+    "gf2x_m128_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
     "gf2x_m128_workspace_bytes": (_SZ, [_U64, _U64]),
     "gf2x_mul_m128": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_m128_encode": (_ST, [_P, _P, _U64, _P, _P]),
@@ -223,6 +225,11 @@ class Context:
                                        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                        self._stream(stream)), "gf2x_mul_m128")
         return out
+
+    def bottom_layers(self, na: int, nb: int, field: int = 64) -> int:
+        """Butterfly layers of an na x nb product done by the fused low-layer kernel."""
+        fn = self._lib.gf2x_m128_bottom_layers if field == 128 else self._lib.gf2x_bottom_layers
+        return int(fn(self._h, na, nb))
 
     def forward_transform(self, b, nb: int, n: int, out=None, workspace=None, stream=None):
         """The transform of b (lines 4-6 of Alg. 5) at transform length n, for reuse."""

@@ -354,12 +354,12 @@ gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 
 // Lines 8-10 of Alg. 5 from the low-layer kernel on: top iButterfly layers,
 // Decode, iBasisCvt, store.
-gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
+gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st, int bt = -1)
 {
     const int l = log2_u64(r.n) - 6;
     const int cnt = r.count;
     const u64 sd = r.stride;
-    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, r.X, l, cnt, sd, st)); }
+    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, r.X, l, cnt, sd, st, bt)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, r.X, l, r.T, cnt, sd, st)); }
     // X is free once Decode has read it: the scratch buffer of iBasisCvt
     { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st)); }
@@ -374,6 +374,8 @@ gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 {
     const int l = log2_u64(r.n) - 6;
+    // X, Y and T are free until the operands are loaded: the tuner's buffers for the bottom-tile depth
+    const int bt = gf2x::butterfly_depth(ctx, r.X, r.Y, r.T, l, r.count, r.stride, st);
     gf2x_status s;
     if (!r.jobs && r.count == 1 && r.La == r.Lb && 2 * r.La <= r.n) {
         s = forward_pair(ctx, r, st);
@@ -385,13 +387,16 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
         if (s != GF2X_OK) return s;
     }
     // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
-    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly_top_pair(ctx, r.X, r.Y, l, r.count, r.stride, st)); }
+    {
+        StageScope g(ctx, STAGE_BUTTERFLY, st);
+        TRY(gf2x::butterfly_top_pair(ctx, r.X, r.Y, l, r.count, r.stride, st, bt));
+    }
     // T is free between Encode and Decode: the tuner's scratch for the low-layer kernel
     {
         StageScope g(ctx, STAGE_BOTTOM, st);
-        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, r.Y, l, r.count, r.stride, st, false, r.T));
+        TRY(gf2x::butterfly_bottom_fused(ctx, r.X, r.Y, l, r.count, r.stride, st, false, r.T, bt));
     }
-    return inverse_tail(ctx, r, st);
+    return inverse_tail(ctx, r, st, bt);
 }
 
 // Lines 4-6 of Alg. 5 on their own: bhat <- Butterfly(Encode(BasisCvt(b)))
@@ -479,6 +484,8 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
     const u64 Lb = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
     const size_t buf = buffer_bytes(n);
     u64 *X = (u64 *)ws, *Y = (u64 *)((char *)ws + buf), *T = (u64 *)((char *)ws + 2 * buf);
+    // X, Y and T are free until the operands are loaded: the tuner's buffers for the bottom-tile depth
+    const int bt = gf2x::m128_butterfly_depth(ctx, X, Y, T, l, 1, 0, st);
     if (La == Lb && 2 * La <= n) {
         // both operands in one launch per stage: a in the lower half of T, b in the upper
         const u64 half = n / 128;
@@ -494,9 +501,12 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
             { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, F, L, 1, 0, 0, st)); }
         }
     }
-    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::m128_butterfly_top_pair(ctx, X, Y, l, 1, 0, st)); }
-    { StageScope g(ctx, STAGE_BOTTOM, st); TRY(gf2x::m128_butterfly_bottom_fused(ctx, X, Y, l, 1, 0, st)); }
-    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::m128_butterfly_top_inverse(ctx, X, l, 1, 0, st)); }
+    { StageScope g(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::m128_butterfly_top_pair(ctx, X, Y, l, 1, 0, st, bt)); }
+    {   // T is free between Encode and Decode: the tuner's scratch for the low-layer kernel
+        StageScope g(ctx, STAGE_BOTTOM, st);
+        TRY(gf2x::m128_butterfly_bottom_fused(ctx, X, Y, l, 1, 0, st, T, bt));
+    }
+    { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::m128_butterfly_top_inverse(ctx, X, l, 1, 0, st, bt)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::m128_decode(ctx, X, l, T, 1, 0, st)); }
     { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st)); }
     { StageScope g(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, product_bits(na, nb), c, st)); }
@@ -882,6 +892,14 @@ gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64
     return op_graph(ctx, OP_MUL, a, na, b, nb, c, ws, (cudaStream_t)stream);
 }
 
+int gf2x_bottom_layers(gf2x_ctx *ctx, uint64_t na, uint64_t nb)
+{
+    if (!ctx) return -1;
+    const u64 n = transform_bits(na, nb);
+    if (!n || n > kMaxTransformBits) return -1;
+    return gf2x::butterfly_depth_stored(ctx, log2_u64(n) - 6, 1);
+}
+
 size_t gf2x_transform_bytes(uint64_t n)
 {
     return valid_n(n) ? (size_t)(n / 8) : 0;
@@ -1068,6 +1086,14 @@ gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b, 
 
 // ------------------------------------------------------------ m = 128
 uint64_t gf2x_m128_transform_bits(uint64_t na, uint64_t nb) { return transform_bits128(na, nb); }
+
+int gf2x_m128_bottom_layers(gf2x_ctx *ctx, uint64_t na, uint64_t nb)
+{
+    if (!ctx) return -1;
+    const u64 n = transform_bits128(na, nb);
+    if (!n || n > kMaxTransformBits128) return -1;
+    return gf2x::m128_butterfly_depth_stored(ctx, log2_u64(n) - 7, 1);
+}
 
 size_t gf2x_m128_workspace_bytes(uint64_t na, uint64_t nb)
 {

@@ -30,8 +30,14 @@
 namespace gf2x {
 namespace {
 
-constexpr int kBottom = 11;          // bottom tile: 2^11 points (16 KiB per transform)
-constexpr int kTableMin = 4;         // bottom layers >= 4 multiply through tables
+#ifndef GF2X_BOTTOM_LAYERS
+#define GF2X_BOTTOM_LAYERS 11        // compile-time override to measure other tile depths
+#endif
+constexpr int kBottom = GF2X_BOTTOM_LAYERS;   // bottom tile: 2^11 points (16 KiB per transform)
+#ifndef GF2X_TABLE_MIN
+#define GF2X_TABLE_MIN 4             // compile-time override to measure other thresholds
+#endif
+constexpr int kTableMin = GF2X_TABLE_MIN;   // bottom layers >= 4 multiply through tables
 constexpr int kTopLayers = 4;        // layers per top pass
 constexpr int kThreads = 256;
 constexpr int kTab = 256;            // u64 entries per multiplication table
@@ -344,13 +350,17 @@ void launch_top(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 
 cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, int count, u64 stride,
                        cudaStream_t st)
 {
-    // passes over layers [bt, l) in groups of <= kTopLayers; high to low for the forward transform
-    const int npass = (l - bt + kTopLayers - 1) / kTopLayers;
+    // passes over layers [bt, l), as few as kTopLayers allows, the layers split
+    // evenly (the lower passes take one more where they do not divide: 9 layers
+    // are 3 + 3 + 3, not 4 + 4 + 1); high to low for the forward transform
+    const int layers = l - bt;
+    const int npass = (layers + kTopLayers - 1) / kTopLayers;
+    const int per = npass ? layers / npass : 0, rem = npass ? layers % npass : 0;
     for (int k = 0; k < npass; ++k) {
         const int idx = inverse ? k : npass - 1 - k;
-        const int p = bt + idx * kTopLayers;
-        const int m = (l - p) < kTopLayers ? (l - p) : kTopLayers;
-        const u64 chunks = (1ull << p) / kThreads;     // p >= kBottom, so 2^p >= 2048 columns
+        const int p = bt + idx * per + (idx < rem ? idx : rem);
+        const int m = per + (idx < rem ? 1 : 0);
+        const u64 chunks = (1ull << p) / kThreads;     // p >= bt >= 9, so 2^p >= 512 columns
         const u64 groups = (1ull << l) >> (p + m);
         // chunks per block: up to 8 (tables built once per block), but keep at
         // least two blocks per SM; a power of two, so it divides `chunks`
@@ -389,13 +399,28 @@ void configure()
 
 }  // namespace
 
+constexpr int kMinDepth = 9;
+
+// The depth used without a measurement: 9 up to l = 21, kBottom above.
+static int default_depth(int l)
+{
+    const int bt = l <= 21 ? kMinDepth : kBottom;
+    return l < bt ? l : bt;
+}
+
+static int depth_or_default(int bt, int l)   // bt < 0: the default depth
+{
+    if (bt < 0) return default_depth(l);
+    return l < bt ? l : bt;
+}
+
 // Forward (or inverse) Butterfly of `count` transforms of 2^l points each,
 // `stride` words apart.
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st,
                       u64 *scratch)
 {
     configure();
-    const int bt = l < kBottom ? l : kBottom;
+    const int bt = default_depth(l);
     if (!inverse) {
         cudaError_t e = top_passes(ctx, x, nullptr, l, bt, false, count, stride, st);
         if (e != cudaSuccess) return e;
@@ -407,32 +432,64 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
     return cudaGetLastError();
 }
 
-// The top layers of both forward transforms (X and Y, or X alone) in one launch per pass.
-cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st)
+
+// Bottom-tile depth for the products of one size class (l, count).  The tuner
+// times the whole schedule (top passes of both forward transforms, the fused
+// bottom kernel, top passes of the inverse) for each depth 9..kBottom on X and
+// Y while they are free, before Encode writes them; the bottom kernel's block
+// shape is tuned for each depth on T (the measurement happens in the untimed
+// first run of the candidate, so the timed runs use the depth's best shape).  A deeper tile moves
+// layers from the HBM passes into shared memory but leaves fewer tiles to
+// spread over the SMs (measured on GB300: 9 is fastest up to 2^24-bit
+// operands, 11 at 2^30); the default without measuring follows that.
+int butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
+{
+    if (l <= kMinDepth) return l;
+    return tune_stored(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | (u64)count, default_depth(l));
+}
+
+int butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st)
 {
     configure();
-    const int bt = l < kBottom ? l : kBottom;
-    return top_passes(ctx, x0, x1, l, bt, false, count, stride, st);
+    if (l <= kMinDepth) return l;
+    const int fallback = default_depth(l);
+    int cands[kBottom];
+    int nc = 0;
+    for (int b = kMinDepth; b <= kBottom && b <= l; ++b) cands[nc++] = b;
+    return tune_choice(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | (u64)count, cands, nc, fallback,
+                       [&](int bt) -> cudaError_t {
+                           cudaError_t e = top_passes(ctx, X, Y, l, bt, false, count, stride, st);
+                           if (e != cudaSuccess) return e;
+                           launch_bottom(ctx, X, Y, l, bt, BOTTOM_FUSED, count, stride, T, st);
+                           return top_passes(ctx, X, nullptr, l, bt, true, count, stride, st);
+                       },
+                       st);
+}
+
+// The top layers of both forward transforms (X and Y, or X alone) in one launch per pass.
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st, int bt)
+{
+    configure();
+    return top_passes(ctx, x0, x1, l, depth_or_default(bt, l), false, count, stride, st);
 }
 
 // Bottom layers of both forward transforms, the pointwise product and the
 // bottom layers of the inverse: X <- low layers of iButterfly(fwd(X) * fwd(Y)).
 // With y_transformed, Y is already a complete forward transform.
 cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
-                                   bool y_transformed, u64 *scratch)
+                                   bool y_transformed, u64 *scratch, int bt)
 {
     configure();
-    const int bt = l < kBottom ? l : kBottom;
+    bt = depth_or_default(bt, l);
     launch_bottom(ctx, X, Y, l, bt, y_transformed ? BOTTOM_FUSED_PRE : BOTTOM_FUSED, count, stride, scratch, st);
     return cudaGetLastError();
 }
 
 // The top layers of the inverse.
-cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st)
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st, int bt)
 {
     configure();
-    const int bt = l < kBottom ? l : kBottom;
-    return top_passes(ctx, x, nullptr, l, bt, true, count, stride, st);
+    return top_passes(ctx, x, nullptr, l, depth_or_default(bt, l), true, count, stride, st);
 }
 
 }  // namespace gf2x

@@ -161,7 +161,10 @@ inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] +
 namespace gf2x {
 
 // Autotuner (tune.cu).  Knobs: the choices it measures.
-enum TuneKnob { TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3 };
+enum TuneKnob {
+    TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3, TUNE_M128_BOTTOM_CHUNK = 4, TUNE_BFLY_DEPTH = 5,
+    TUNE_M128_BFLY_DEPTH = 6
+};
 void *tuner_create();
 void tuner_destroy(void *t);
 // The stored choice for (knob, key); else, when measuring is possible, runs
@@ -169,6 +172,8 @@ void tuner_destroy(void *t);
 // else `fallback`.
 int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, int fallback,
                 const std::function<cudaError_t(int)> &run, cudaStream_t st);
+// The stored choice for (knob, key), else `fallback`; never measures.
+int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback);
 
 // Batched forms: `count` jobs whose buffers are `stride` words apart
 // (count = 1, stride = 0 for a single product).
@@ -194,10 +199,17 @@ cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u6
 // scratch (nullable): a free buffer of the transform's size, for the tuner.
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st,
                       u64 *scratch = nullptr);
-cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
+// Bottom-tile depth bt for products with 2^l points, measured on X, Y and T
+// (free buffers laid out like the transforms).  The three calls below take it
+// (bt < 0: the default depth); one product uses the same bt in all three.
+int butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st);
+// The depth butterfly_depth returned (or would return without measuring).
+int butterfly_depth_stored(gf2x_ctx *ctx, int l, int count);
+cudaError_t butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st,
+                               int bt = -1);
 cudaError_t butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int count, u64 stride, cudaStream_t st,
-                                   bool y_transformed = false, u64 *scratch = nullptr);
-cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
+                                   bool y_transformed = false, u64 *scratch = nullptr, int bt = -1);
+cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st, int bt = -1);
 cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u64 stride, u64 dst_words, int count,
                       cudaStream_t st);
 cudaError_t store_jobs(gf2x_ctx *ctx, const u64 *src, u64 stride, const JobDev *jobs, u64 max_words, int count,
@@ -223,10 +235,16 @@ cudaError_t m128_encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonz
                         u64 out_stride, cudaStream_t st);
 cudaError_t m128_decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st);
 cudaError_t m128_butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st);
-cudaError_t m128_butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st);
+// Bottom-tile depth, as butterfly_depth / butterfly_depth_stored for m = 64.
+int m128_butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st);
+int m128_butterfly_depth_stored(gf2x_ctx *ctx, int l, int count);
+cudaError_t m128_butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st,
+                                    int bt = -1);
+// scratch (nullable): a free buffer laid out like X, for the tuner.
 cudaError_t m128_butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int count, u64 stride,
-                                        cudaStream_t st);
-cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st);
+                                        cudaStream_t st, u64 *scratch = nullptr, int bt = -1);
+cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st,
+                                       int bt = -1);
 cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
 
 }  // namespace gf2x

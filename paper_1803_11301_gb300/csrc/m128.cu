@@ -30,21 +30,25 @@ namespace {
 #define GF2X_M128_BOTTOM 10
 #endif
 #ifndef GF2X_M128_TABLE_MIN
-#define GF2X_M128_TABLE_MIN 4
+#define GF2X_M128_TABLE_MIN 5
 #endif
 #ifndef GF2X_M128_TOP
 #define GF2X_M128_TOP 3
 #endif
-#ifndef GF2X_M128_CHUNK
-#define GF2X_M128_CHUNK 4
-#endif
 constexpr u64 kMod128Low = 0x87;      // x^7 + x^2 + x + 1
-constexpr int kBottom128 = GF2X_M128_BOTTOM;       // bottom tile: 2^10 points (16 KiB per transform)
-constexpr int kTableMin128 = GF2X_M128_TABLE_MIN;  // bottom layers >= 4 multiply through tables
+constexpr int kBottom128 = GF2X_M128_BOTTOM;       // deepest bottom tile: 2^10 points (16 KiB per transform)
+// Bottom layers >= 5 multiply through tables, lower ones with the integer
+// product: a 128-bit table costs ~4600 instructions to build and layer 4 uses
+// each one 48 times (measured on GB300: threshold 5 is 3% faster than 4 at
+// 2^24 and 2^30-bit operands, 3 is 10% slower).
+constexpr int kTableMin128 = GF2X_M128_TABLE_MIN;
 constexpr int kTopLayers128 = GF2X_M128_TOP;       // layers per top pass (<= 4)
 constexpr int kThreads128 = 256;
 constexpr int kTab128 = 1024;         // u64 words per multiplication table (8 KiB)
-constexpr int kChunk128 = GF2X_M128_CHUNK;         // tables built at a time in the bottom tile
+// Tables built at a time in the bottom tile: 4 (64 KiB of shared memory, 3
+// blocks per SM) or 8 (96 KiB, 2 blocks per SM, fewer barriers); the tuner
+// measures both per launch shape (4 won at 2^30-bit operands, 8 at 2^24).
+constexpr int kChunkSmall128 = 4, kChunkLarge128 = 8;
 constexpr int kCols128 = 16;          // word columns per Encode/Decode block
 constexpr int kPad128 = kCols128 + 1;
 constexpr int kLinWords = 16 * 256 * 2;  // words of a 128-bit byte-window table
@@ -414,16 +418,17 @@ __device__ __forceinline__ void tile_layer128(u64 *a, int bt, int i, g128 ctop, 
 }
 
 // Layer i >= kTableMin128 on the tile(s): the 2^(bt-1-i) twiddles
-// c_j = v_{l+64-i} + Cantor((base >> i) + 2j) get tables kChunk128 at a time;
+// c_j = v_{l+64-i} + Cantor((base >> i) + 2j) get tables CHUNK at a time;
 // each chunk's butterflies run on a and, if given, b.
+template <int CHUNK>
 __device__ void table_layer128(u64 *a, u64 *b, int bt, int i, int l, u64 base, const u64 *__restrict__ cvt,
                                const u64 *__restrict__ vb, u64 *tabs, bool inverse)
 {
     const int ntot = 1 << (bt - 1 - i);
     const int span = 1 << i;
     const g128 vtop = ld128(vb + 2 * (l + 64 - i));
-    for (int j0 = 0; j0 < ntot; j0 += kChunk128) {
-        const int nt = ntot - j0 < kChunk128 ? ntot - j0 : kChunk128;
+    for (int j0 = 0; j0 < ntot; j0 += CHUNK) {
+        const int nt = ntot - j0 < CHUNK ? ntot - j0 : CHUNK;
         build_tables128(tabs, nt, [&](int t) { return gx(vtop, cantor128(cvt, (base >> i) + ((u64)(j0 + t) << 1))); });
         for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
             const int blk = j0 + (t >> i), jj = t & (span - 1);
@@ -458,6 +463,7 @@ __host__ __device__ __forceinline__ int tile_words128(int bt) { return (2 << bt)
 // One tile of 2^bt points per block: the low layers of the forward transform
 // (of X, and of Y in the fused mode), then in the fused mode the pointwise
 // product X * Y (Alg. 5 line 7), then the low layers of the inverse.
+template <int CHUNK>
 __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u64 *Y, int l, int bt,
                                                                 const u64 *__restrict__ cvt, const u64 *__restrict__ vb,
                                                                 int mode, u64 stride)
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u6
     if (mode != B128_INV) {
         for (int i = bt - 1; i >= 0; --i) {
             if (i >= kTableMin128) {
-                table_layer128(a, b, bt, i, l, base, cvt, vb, tabs, false);
+                table_layer128<CHUNK>(a, b, bt, i, l, base, cvt, vb, tabs, false);
             } else {
                 const g128 ctop = gx(ld128(vb + 2 * (l + 64 - i)), cantor128(cvt, base >> i));
                 tile_layer128(a, bt, i, ctop, cvt, false);
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u6
     if (mode != B128_FWD) {
         for (int i = 0; i < bt; ++i) {
             if (i >= kTableMin128) {
-                table_layer128(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
+                table_layer128<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
             } else {
                 const g128 ctop = gx(ld128(vb + 2 * (l + 64 - i)), cantor128(cvt, base >> i));
                 tile_layer128(a, bt, i, ctop, cvt, true);
@@ -507,9 +513,9 @@ __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u6
     for (int k = threadIdx.x; k < T; k += blockDim.x) st128(X + 2 * (base + k), ld128(a + 2 * k));
 }
 
-size_t bottom_smem128(int bt, bool fused)
+size_t bottom_smem128(int bt, bool fused, int chunk)
 {
-    return ((fused ? 2 : 1) * (size_t)tile_words128(bt) + (size_t)kChunk128 * kTab128) * sizeof(u64) + 128;
+    return ((fused ? 2 : 1) * (size_t)tile_words128(bt) + (size_t)chunk * kTab128) * sizeof(u64) + 128;
 }
 
 size_t top_smem128(int m) { return (size_t)((1 << m) - 1) * kTab128 * sizeof(u64) + 128; }
@@ -521,8 +527,10 @@ bool configured128 = false;
 void configure128()
 {
     if (configured128) return;
-    cudaFuncSetAttribute(k128_bfly_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bottom_smem128(kBottom128, true));
+    cudaFuncSetAttribute(k128_bfly_bottom<kChunkSmall128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bottom_smem128(kBottom128, true, kChunkSmall128));
+    cudaFuncSetAttribute(k128_bfly_bottom<kChunkLarge128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bottom_smem128(kBottom128, true, kChunkLarge128));
     cudaFuncSetAttribute(k128_bfly_top<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)top_smem128(3));
     cudaFuncSetAttribute(k128_bfly_top<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)top_smem128(3));
     cudaFuncSetAttribute(k128_bfly_top<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)top_smem128(4));
@@ -540,17 +548,20 @@ void launch_top128(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u
                                                                       stride);
 }
 
-// Passes over layers [bt, l) in groups of <= kTopLayers128, high to low for
-// the forward transform.  p >= bt = kBottom128, so a group has >= 2^10
-// columns, a multiple of the block size.
+// Passes over layers [bt, l), as few as kTopLayers128 allows, the layers split
+// evenly (lower passes take one more where they do not divide), high to low
+// for the forward transform.  p >= bt >= 8, so a group has >= 256 columns, a
+// multiple of the block size.
 cudaError_t top_passes128(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, int count, u64 stride,
                           cudaStream_t st)
 {
-    const int npass = (l - bt + kTopLayers128 - 1) / kTopLayers128;
+    const int layers = l - bt;
+    const int npass = (layers + kTopLayers128 - 1) / kTopLayers128;
+    const int per = npass ? layers / npass : 0, rem = npass ? layers % npass : 0;
     for (int k = 0; k < npass; ++k) {
         const int idx = inverse ? k : npass - 1 - k;
-        const int p = bt + idx * kTopLayers128;
-        const int m = (l - p) < kTopLayers128 ? (l - p) : kTopLayers128;
+        const int p = bt + idx * per + (idx < rem ? idx : rem);
+        const int m = per + (idx < rem ? 1 : 0);
         const u64 chunks = (1ull << p) / kThreads128;
         const u64 groups = (1ull << l) >> (p + m);
         const int arrays = x1 ? 2 : 1;
@@ -574,15 +585,37 @@ cudaError_t top_passes128(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool i
     return cudaGetLastError();
 }
 
-cudaError_t launch_bottom128(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int mode, int count, u64 stride,
-                             cudaStream_t st)
+cudaError_t launch_bottom128_chunk(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int bt, int mode, int count,
+                                   u64 stride, int chunk, cudaStream_t st)
 {
-    const int bt = l < kBottom128 ? l : kBottom128;
     const dim3 grid((unsigned)(1ull << (l - bt)), count);
-    k128_bfly_bottom<<<grid, kThreads128, bottom_smem128(bt, mode == B128_FUSED), st>>>(
-        X, Y, l, bt, ctx->d_cvt128, ctx->d_cantor128, mode, stride);
+    const size_t smem = bottom_smem128(bt, mode == B128_FUSED, chunk);
+    if (chunk == kChunkLarge128)
+        k128_bfly_bottom<kChunkLarge128><<<grid, kThreads128, smem, st>>>(X, Y, l, bt, ctx->d_cvt128,
+                                                                           ctx->d_cantor128, mode, stride);
+    else
+        k128_bfly_bottom<kChunkSmall128><<<grid, kThreads128, smem, st>>>(X, Y, l, bt, ctx->d_cvt128,
+                                                                           ctx->d_cantor128, mode, stride);
     count_launch(ctx);
     return cudaGetLastError();
+}
+
+// The chunk measured by the tuner on `scratch` (a free buffer laid out like X;
+// Y is only read), or the default without one.
+cudaError_t launch_bottom128(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int bt, int mode, int count, u64 stride,
+                             u64 *scratch, cudaStream_t st)
+{
+    const u64 tiles = (1ull << (l - bt)) * (u64)count;
+    int chunk = tiles > 2 * (u64)ctx->num_sms ? kChunkSmall128 : kChunkLarge128;
+    if (scratch) {
+        static const int cands[2] = {kChunkLarge128, kChunkSmall128};
+        chunk = tune_choice(ctx, TUNE_M128_BOTTOM_CHUNK, (tiles << 2) | (u64)mode, cands, 2, chunk,
+                            [&](int ch) {
+                                return launch_bottom128_chunk(ctx, scratch, Y, l, bt, mode, count, stride, ch, st);
+                            },
+                            st);
+    }
+    return launch_bottom128_chunk(ctx, X, Y, l, bt, mode, count, stride, chunk, st);
 }
 
 // ------------------------------------------------------------ host set-up
@@ -737,41 +770,85 @@ cudaError_t m128_decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int coun
     return cudaGetLastError();
 }
 
+// Bottom-tile depth: measured per (l, count) by m128_butterfly_depth, else 9
+// up to l = 20 and kBottom128 above (measured on GB300: 9 is fastest at
+// 2^24-bit operands, 10 at 2^30).
+constexpr int kMinDepth128 = 8;
+
+static int default_depth128(int l)
+{
+    const int bt = l <= 20 ? 9 : kBottom128;
+    return l < bt ? l : bt;
+}
+
+static int depth_or_default128(int bt, int l)   // bt < 0: the default depth
+{
+    if (bt < 0) return default_depth128(l);
+    return l < bt ? l : bt;
+}
+
+int m128_butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
+{
+    if (l <= kMinDepth128) return l;
+    return tune_stored(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | (u64)count, default_depth128(l));
+}
+
+// The whole schedule (top passes of both forward transforms, fused bottom
+// kernel, top passes of the inverse) timed per depth on the free X and Y, the
+// bottom kernel's table chunk tuned per depth on T (in the untimed first run).
+int m128_butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st)
+{
+    configure128();
+    if (l <= kMinDepth128) return l;
+    int cands[kBottom128];
+    int nc = 0;
+    for (int b = kMinDepth128; b <= kBottom128 && b <= l; ++b) cands[nc++] = b;
+    return tune_choice(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | (u64)count, cands, nc, default_depth128(l),
+                       [&](int bt) -> cudaError_t {
+                           cudaError_t e = top_passes128(ctx, X, Y, l, bt, false, count, stride, st);
+                           if (e != cudaSuccess) return e;
+                           e = launch_bottom128(ctx, X, Y, l, bt, B128_FUSED, count, stride, T, st);
+                           if (e != cudaSuccess) return e;
+                           return top_passes128(ctx, X, nullptr, l, bt, true, count, stride, st);
+                       },
+                       st);
+}
+
 cudaError_t m128_butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st)
 {
     configure128();
-    const int bt = l < kBottom128 ? l : kBottom128;
+    const int bt = default_depth128(l);
     if (!inverse) {
         cudaError_t e = top_passes128(ctx, x, nullptr, l, bt, false, count, stride, st);
         if (e != cudaSuccess) return e;
     }
     if (bt > 0) {
-        cudaError_t e = launch_bottom128(ctx, x, nullptr, l, inverse ? B128_INV : B128_FWD, count, stride, st);
+        cudaError_t e =
+            launch_bottom128(ctx, x, nullptr, l, bt, inverse ? B128_INV : B128_FWD, count, stride, nullptr, st);
         if (e != cudaSuccess) return e;
     }
     if (inverse) return top_passes128(ctx, x, nullptr, l, bt, true, count, stride, st);
     return cudaGetLastError();
 }
 
-cudaError_t m128_butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st)
+cudaError_t m128_butterfly_top_pair(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int count, u64 stride, cudaStream_t st,
+                                    int bt)
 {
     configure128();
-    const int bt = l < kBottom128 ? l : kBottom128;
-    return top_passes128(ctx, x0, x1, l, bt, false, count, stride, st);
+    return top_passes128(ctx, x0, x1, l, depth_or_default128(bt, l), false, count, stride, st);
 }
 
 cudaError_t m128_butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int count, u64 stride,
-                                        cudaStream_t st)
+                                        cudaStream_t st, u64 *scratch, int bt)
 {
     configure128();
-    return launch_bottom128(ctx, X, Y, l, B128_FUSED, count, stride, st);
+    return launch_bottom128(ctx, X, Y, l, depth_or_default128(bt, l), B128_FUSED, count, stride, scratch, st);
 }
 
-cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st)
+cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st, int bt)
 {
     configure128();
-    const int bt = l < kBottom128 ? l : kBottom128;
-    return top_passes128(ctx, x, nullptr, l, bt, true, count, stride, st);
+    return top_passes128(ctx, x, nullptr, l, depth_or_default128(bt, l), true, count, stride, st);
 }
 
 cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st)

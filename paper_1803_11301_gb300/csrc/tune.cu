@@ -4,12 +4,13 @@
 // in speed, with the best one depending on the size (how many blocks a launch
 // has against the SM count): the words per thread of the 2^16-bit BasisCvt
 // kernel, the block shape of the fused bottom butterfly, the depth of the
-// Taylor window kernel.  The first time a call meets a new (knob, key), and
+// Taylor window kernel, the table chunk of the GF(2^128) bottom butterfly.  The first time a call meets a new (knob, key), and
 // the stream is not being captured, the tuner runs every candidate a few
 // times on a scratch buffer of the same layout (contents are garbage; every
 // kernel's indexing is independent of the data), takes the fastest by CUDA
 // events on the launching stream, and remembers it in the context.  Later
 // calls, including the CUDA graphs captured from them, use the stored choice.
+// The built-in default is kept unless a candidate is more than 3% faster.
 // GF2X_TUNE=0 in the environment turns measuring off (the built-in defaults
 // are then used).  The first call of a new shape synchronises its stream.
 #include <cstdlib>
@@ -33,7 +34,9 @@ struct TuneCache {
 
 TuneCache *cache(gf2x_ctx *ctx) { return (TuneCache *)ctx->tuner; }
 
-constexpr int kReps = 3;
+constexpr int kReps = 5;
+constexpr float kMargin = 0.03f;
+
 
 }  // namespace
 
@@ -46,6 +49,15 @@ void *tuner_create()
 }
 
 void tuner_destroy(void *t) { delete (TuneCache *)t; }
+
+int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback)
+{
+    TuneCache *c = cache(ctx);
+    if (c)
+        for (const TuneEntry &e : c->entries)
+            if (e.knob == knob && e.key == key) return e.choice;
+    return fallback;
+}
 
 int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, int fallback,
                 const std::function<cudaError_t(int)> &run, cudaStream_t st)
@@ -65,23 +77,30 @@ int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, i
     }
     unsigned long long saved[STAGE_COUNT];           // measuring launches are not the caller's
     for (int k = 0; k < STAGE_COUNT; ++k) saved[k] = ctx->launches[k];
-    int best = fallback;
-    float best_ms = 0;
+    // one untimed run of every candidate (first launches load the kernels and
+    // warm the caches), then kReps rounds over all candidates, interleaved so
+    // that drift of the clock or of other work on the GPU touches all alike;
+    // each candidate keeps its fastest round
     bool ok = true;
-    for (int i = 0; i < ncand && ok; ++i) {
-        float cand_ms = 0;
-        for (int rep = 0; rep < kReps && ok; ++rep) {
+    for (int i = 0; i < ncand && ok; ++i) ok = run(cands[i]) == cudaSuccess;
+    std::vector<float> cand_ms((size_t)ncand, 0.0f);
+    for (int rep = 0; rep < kReps && ok; ++rep) {
+        for (int i = 0; i < ncand && ok; ++i) {
             ok = cudaEventRecord(e0, st) == cudaSuccess && run(cands[i]) == cudaSuccess &&
                  cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0;
             if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-            if (ok && (rep == 0 || ms < cand_ms)) cand_ms = ms;
-        }
-        if (ok && (i == 0 || cand_ms < best_ms)) {
-            best_ms = cand_ms;
-            best = cands[i];
+            if (ok && (rep == 0 || ms < cand_ms[(size_t)i])) cand_ms[(size_t)i] = ms;
         }
     }
+    // the default stays unless a candidate beats it by more than kMargin:
+    // choices within the run-to-run noise would otherwise flip between runs
+    int best_i = 0;
+    for (int i = 1; i < ncand; ++i)
+        if (cand_ms[(size_t)i] < cand_ms[(size_t)best_i]) best_i = i;
+    for (int i = 0; i < ncand; ++i)
+        if (cands[i] == fallback && cand_ms[(size_t)i] <= (1.0f + kMargin) * cand_ms[(size_t)best_i]) best_i = i;
+    const int best = cands[best_i];
     for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] = saved[k];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
