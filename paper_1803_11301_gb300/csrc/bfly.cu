@@ -38,7 +38,13 @@ constexpr int kBottom = GF2X_BOTTOM_LAYERS;   // bottom tile: 2^11 points (16 Ki
 #define GF2X_TABLE_MIN 4             // compile-time override to measure other thresholds
 #endif
 constexpr int kTableMin = GF2X_TABLE_MIN;   // bottom layers >= 4 multiply through tables
-constexpr int kTopLayers = 4;        // layers per top pass
+// Layers per top pass (<= 4; compile-time override to measure others).  On
+// GB300, 3 measured 1.6% faster at 2^30-bit operands and even at 2^24; 5 (176
+// to 255 registers, one block per SM) 10% slower.
+#ifndef GF2X_TOP_LAYERS
+#define GF2X_TOP_LAYERS 4
+#endif
+constexpr int kTopLayers = GF2X_TOP_LAYERS;
 constexpr int kThreads = 256;
 constexpr int kTab = 256;            // u64 entries per multiplication table
 
