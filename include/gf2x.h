@@ -208,6 +208,14 @@ GF2X_API gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream);
  * traps. */
 GF2X_API gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream);
 
+/* Launch shapes (bottom-tile depth, block shapes, table chunks, BasisCvt
+ * words per thread) are measured on first use of each shape class, which
+ * synchronises the stream once; later calls reuse the choice.  With
+ * frozen != 0 the context measures nothing new (stored choices, else the
+ * built-in defaults): for servers, after a warm-up.  frozen = 0 resumes.
+ * GF2X_TUNE=0 in the environment at context creation never measures. */
+GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
+
 /* Butterfly layers (Alg. 2) that gf2x_mul runs in its fused low-layer kernel
  * for an na x nb product, the rest running as passes over HBM: the depth the
  * context's tuner measured at the first product of this transform length, or

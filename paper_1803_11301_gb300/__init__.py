@@ -56,6 +56,7 @@ ABI_FUNCTIONS = {
     "gf2x_ibutterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
     "gf2x_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
+    "gf2x_tune_freeze": (_ST, [_P, ctypes.c_int]),
     "gf2x_m128_transform_bits": (_U64, [_U64, _U64]),
     "gf2x_m128_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
     "gf2x_m128_workspace_bytes": (_SZ, [_U64, _U64]),
@@ -225,6 +226,10 @@ class Context:
                                        ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                        self._stream(stream)), "gf2x_mul_m128")
         return out
+
+    def tune_freeze(self, frozen: bool = True):
+        """Stop (or resume) measuring launch shapes on first use; stored choices stay."""
+        _check(self._lib.gf2x_tune_freeze(self._h, 1 if frozen else 0), "gf2x_tune_freeze")
 
     def bottom_layers(self, na: int, nb: int, field: int = 64) -> int:
         """Butterfly layers of an na x nb product done by the fused low-layer kernel."""

@@ -892,6 +892,13 @@ gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64
     return op_graph(ctx, OP_MUL, a, na, b, nb, c, ws, (cudaStream_t)stream);
 }
 
+gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen)
+{
+    if (!ctx) return GF2X_EINVAL;
+    gf2x::tuner_freeze(ctx->tuner, frozen != 0);
+    return GF2X_OK;
+}
+
 int gf2x_bottom_layers(gf2x_ctx *ctx, uint64_t na, uint64_t nb)
 {
     if (!ctx) return -1;

@@ -338,7 +338,7 @@ void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int c
     int shape = tiles * (u64)count < 4 * (u64)ctx->num_sms ? 1 : 0;
     if (scratch) {
         static const int cands[2] = {1, 0};
-        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, ((tiles * (u64)count) << 2) | (u64)mode, cands, 2, shape,
+        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, (tune_bucket(tiles * (u64)count) << 2) | (u64)mode, cands, 2, shape,
                             [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, st); },
                             st);
     }
@@ -366,7 +366,7 @@ cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inve
         const int idx = inverse ? k : npass - 1 - k;
         const int p = bt + idx * per + (idx < rem ? idx : rem);
         const int m = per + (idx < rem ? 1 : 0);
-        const u64 chunks = (1ull << p) / kThreads;     // p >= bt >= 9, so 2^p >= 512 columns
+        const u64 chunks = (1ull << p) / kThreads;     // p >= bt >= 8, so 2^p >= 256 columns
         const u64 groups = (1ull << l) >> (p + m);
         // chunks per block: up to 8 (tables built once per block), but keep at
         // least two blocks per SM; a power of two, so it divides `chunks`
@@ -405,12 +405,12 @@ void configure()
 
 }  // namespace
 
-constexpr int kMinDepth = 9;
+constexpr int kMinDepth = 8;              // shallowest depth the tuner tries
 
 // The depth used without a measurement: 9 up to l = 21, kBottom above.
 static int default_depth(int l)
 {
-    const int bt = l <= 21 ? kMinDepth : kBottom;
+    const int bt = l <= 21 ? 9 : kBottom;
     return l < bt ? l : bt;
 }
 
@@ -441,7 +441,7 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
 
 // Bottom-tile depth for the products of one size class (l, count).  The tuner
 // times the whole schedule (top passes of both forward transforms, the fused
-// bottom kernel, top passes of the inverse) for each depth 9..kBottom on X and
+// bottom kernel, top passes of the inverse) for each depth 8..kBottom on X and
 // Y while they are free, before Encode writes them; the bottom kernel's block
 // shape is tuned for each depth on T (the measurement happens in the untimed
 // first run of the candidate, so the timed runs use the depth's best shape).  A deeper tile moves
@@ -451,7 +451,7 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
 int butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
 {
     if (l <= kMinDepth) return l;
-    return tune_stored(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | (u64)count, default_depth(l));
+    return tune_stored(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth(l));
 }
 
 int butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st)
@@ -462,7 +462,7 @@ int butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64
     int cands[kBottom];
     int nc = 0;
     for (int b = kMinDepth; b <= kBottom && b <= l; ++b) cands[nc++] = b;
-    return tune_choice(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | (u64)count, cands, nc, fallback,
+    return tune_choice(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), cands, nc, fallback,
                        [&](int bt) -> cudaError_t {
                            cudaError_t e = top_passes(ctx, X, Y, l, bt, false, count, stride, st);
                            if (e != cudaSuccess) return e;

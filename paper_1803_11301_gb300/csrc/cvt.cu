@@ -627,7 +627,7 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
     if (m > 6) {
         static const int cands[3] = {6, 7, 8};
         const int top = m < 8 ? m : 8;
-        cap = tune_choice(ctx, TUNE_WINDOW_DEPTH, ((u64)K << 33) | ((u64)count << 1) | (inverse ? 1u : 0u), cands,
+        cap = tune_choice(ctx, TUNE_WINDOW_DEPTH, ((u64)K << 33) | (tune_bucket((u64)count) << 1) | (inverse ? 1u : 0u), cands,
                           top - 5, cap, [&](int c) -> cudaError_t {
                               std::vector<Step> w;
                               for (int k = top - 1; k >= c; --k) w.push_back({1ull << (16 + k), 1ull << k});

@@ -167,11 +167,21 @@ enum TuneKnob {
 };
 void *tuner_create();
 void tuner_destroy(void *t);
+void tuner_freeze(void *t, bool frozen);
 // The stored choice for (knob, key); else, when measuring is possible, runs
 // run(candidate) on `st` for every candidate, stores and returns the fastest;
 // else `fallback`.
 int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, int fallback,
                 const std::function<cudaError_t(int)> &run, cudaStream_t st);
+// Keys use the power-of-two bucket of a count (ceil(log2 x)): the best shape
+// depends on the amount of work, so one measurement serves every count of a
+// bucket (batches and serving meet many distinct job counts).
+inline u64 tune_bucket(u64 x)
+{
+    u64 b = 0;
+    while (b < 63 && (1ull << b) < x) ++b;
+    return b;
+}
 // The stored choice for (knob, key), else `fallback`; never measures.
 int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback);
 

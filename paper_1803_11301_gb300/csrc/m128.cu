@@ -609,7 +609,7 @@ cudaError_t launch_bottom128(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int bt,
     int chunk = tiles > 2 * (u64)ctx->num_sms ? kChunkSmall128 : kChunkLarge128;
     if (scratch) {
         static const int cands[2] = {kChunkLarge128, kChunkSmall128};
-        chunk = tune_choice(ctx, TUNE_M128_BOTTOM_CHUNK, (tiles << 2) | (u64)mode, cands, 2, chunk,
+        chunk = tune_choice(ctx, TUNE_M128_BOTTOM_CHUNK, (tune_bucket(tiles) << 2) | (u64)mode, cands, 2, chunk,
                             [&](int ch) {
                                 return launch_bottom128_chunk(ctx, scratch, Y, l, bt, mode, count, stride, ch, st);
                             },
@@ -790,7 +790,7 @@ static int depth_or_default128(int bt, int l)   // bt < 0: the default depth
 int m128_butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
 {
     if (l <= kMinDepth128) return l;
-    return tune_stored(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | (u64)count, default_depth128(l));
+    return tune_stored(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth128(l));
 }
 
 // The whole schedule (top passes of both forward transforms, fused bottom
@@ -803,7 +803,7 @@ int m128_butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count
     int cands[kBottom128];
     int nc = 0;
     for (int b = kMinDepth128; b <= kBottom128 && b <= l; ++b) cands[nc++] = b;
-    return tune_choice(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | (u64)count, cands, nc, default_depth128(l),
+    return tune_choice(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), cands, nc, default_depth128(l),
                        [&](int bt) -> cudaError_t {
                            cudaError_t e = top_passes128(ctx, X, Y, l, bt, false, count, stride, st);
                            if (e != cudaSuccess) return e;

@@ -12,7 +12,8 @@
 // calls, including the CUDA graphs captured from them, use the stored choice.
 // The built-in default is kept unless a candidate is more than 3% faster.
 // GF2X_TUNE=0 in the environment turns measuring off (the built-in defaults
-// are then used).  The first call of a new shape synchronises its stream.
+// are then used); gf2x_tune_freeze stops it for one context (a server tunes
+// during its warm-up, then freezes so that no request waits on a measurement).  The first call of a new shape synchronises its stream.
 #include <cstdlib>
 #include <vector>
 
@@ -29,7 +30,8 @@ struct TuneEntry {
 
 struct TuneCache {
     std::vector<TuneEntry> entries;
-    bool disabled = false;
+    bool disabled = false;    // GF2X_TUNE=0: never measure
+    bool frozen = false;      // gf2x_tune_freeze: stored choices and defaults only
 };
 
 TuneCache *cache(gf2x_ctx *ctx) { return (TuneCache *)ctx->tuner; }
@@ -50,6 +52,11 @@ void *tuner_create()
 
 void tuner_destroy(void *t) { delete (TuneCache *)t; }
 
+void tuner_freeze(void *t, bool frozen)
+{
+    if (t) ((TuneCache *)t)->frozen = frozen;
+}
+
 int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback)
 {
     TuneCache *c = cache(ctx);
@@ -67,7 +74,8 @@ int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, i
     for (const TuneEntry &e : c->entries)
         if (e.knob == knob && e.key == key) return e.choice;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (c->disabled || ncand < 2 || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    if (c->disabled || c->frozen || ncand < 2 || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
         return fallback;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return fallback;

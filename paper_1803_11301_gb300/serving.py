@@ -10,6 +10,11 @@ on another stream, so their work overlaps on the device; a batch is complete
 when its event has fired.  Latency of a request = completion time - arrival
 time, both on the host clock.
 
+The library measures launch shapes the first time it meets a shape class,
+which stalls that batch's stream; a server warms up on a representative mix
+and then calls ``Context.tune_freeze()`` so that no request waits on a
+measurement.
+
 This module only schedules: every product runs in the library's kernels.
 """
 

@@ -374,3 +374,29 @@ def test_forward_transform_is_evaluation_at_sigma(ctx):
     y = host(ctx.forward_transform(dev(b), nb, n))
     for k in sorted({0, 1, (1 << l) - 1} | {rng.randrange(1 << l) for _ in range(5)}):
         assert int(y[k]) == O.eval_at(synth.mask_tail(b.copy(), nb), nb, S.sigma_point(l, k)), k
+
+
+def test_default_launch_shapes_without_tuning(ctx):
+    # GF2X_TUNE=0: the built-in shapes (bottom depth 9 up to l = 21, 11 above), same products
+    import os
+    from paper_1803_11301_gb300 import Context
+    old = os.environ.get("GF2X_TUNE")
+    os.environ["GF2X_TUNE"] = "0"
+    try:
+        c0 = Context(0)
+    finally:
+        if old is None:
+            del os.environ["GF2X_TUNE"]
+        else:
+            os.environ["GF2X_TUNE"] = old
+    try:
+        for na, nb in [(1 << 18, 1 << 18), (1 << 22, 1 << 21), (123457, 1 << 20)]:
+            a = synth.operand(synth.config_seed(9, na), na)
+            b = synth.operand(synth.config_seed(9, nb + 7), nb)
+            got = host(c0.mul(dev(a), na, dev(b), nb))
+            assert np.array_equal(got, O.mul(a, na, b, nb)), (na, nb)
+            l = S.transform_length(na, nb).bit_length() - 1 - 6
+            assert c0.bottom_layers(na, nb) == min(l, 9 if l <= 21 else 11)
+            assert 8 <= ctx.bottom_layers(na, nb) <= 11          # the tuned context's choice
+    finally:
+        c0.close()
