@@ -676,6 +676,32 @@ cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, 
     if (scratch && K >= 18 && K <= 32) return basis_cvt_structured(ctx, bits, scratch, L, K, inverse, count, stride, st);
     std::vector<Step> steps;
     build_steps(K, 1, steps);
+    if (scratch && K > 32) {
+        // Alg. 1 with i = 32 (tau = 2^32): its K - 32 Taylor layers and the outer
+        // conversion of the 2^(K-32) units of 2^32 bits are the generic steps
+        // before the last |build_steps(32)| ones; those are the inner conversion
+        // of every unit, run by the structured K = 32 path (outer and inner commute).
+        std::vector<Step> inner;
+        build_steps(32, 1, inner);
+        steps.resize(steps.size() - inner.size());
+        const u64 unit_words = 1ull << 26, units = L >> 32;
+        auto inner_all = [&]() -> cudaError_t {
+            if (count == 1 || stride == units * unit_words)
+                return basis_cvt_structured(ctx, bits, scratch, 1ull << 32, 32, inverse, (int)(units * (u64)count),
+                                            unit_words, st);
+            for (int j = 0; j < count; ++j)
+                TRY_CUDA(basis_cvt_structured(ctx, bits + (u64)j * stride, scratch + (u64)j * stride, 1ull << 32, 32,
+                                              inverse, (int)units, unit_words, st));
+            return cudaSuccess;
+        };
+        if (inverse) {
+            TRY_CUDA(inner_all());
+            return run_steps_generic(ctx, bits, bits, L, std::vector<Step>(steps.rbegin(), steps.rend()), true, count,
+                                     stride, st);
+        }
+        TRY_CUDA(run_steps_generic(ctx, bits, bits, L, steps, false, count, stride, st));
+        return inner_all();
+    }
     if (steps.empty()) return cudaSuccess;
     // For K >= 16 the list ends with the 32 steps of BasisCvt inside every
     // 2^16-bit block, run by the register kernel (first for the inverse, last
