@@ -153,26 +153,41 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ distributed
-def dist_setup(n_gpus):
+# Multi-GPU: replicas only.  Each rank multiplies its own operands (its own
+# seed); the only cross-rank calls are a barrier around the timed region and
+# the max-reduction of the timed seconds.  backend="gloo" / device="cpu" run
+# the same code on CPU processes (tests); the bench uses NCCL on the GPUs.
+def dist_setup(n_gpus, backend: str = "nccl"):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
-def dist_max(x: float, world: int) -> float:
+def dist_max(x: float, world: int, device: str = "cuda") -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(config: int, rank: int) -> int:
+    """Operand seed of a rank: every replica multiplies different operands."""
+    return synth.config_seed(config, 1000 + 17 * rank)
+
+
+def whole_job_value(units_per_rank: float, seconds_max: float, world: int, scale: float = 1e9) -> float:
+    """Weak-scaling throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / seconds_max / scale
 
 
 def dist_barrier(world):
@@ -338,7 +353,7 @@ def run_gpu(args, world, rank, local):
     nc = na + nb - 1
     ctx = Context(local)
     stream = torch.cuda.current_stream(dev)
-    seed = synth.config_seed(args.config, 1000 + 17 * rank)
+    seed = replica_seed(args.config, rank)
     a_h = synth.operand(seed, na)
     b_h = synth.operand(seed + 1, nb)
     a = torch.from_numpy(a_h.view(np.int64)).to(dev)
@@ -396,7 +411,7 @@ def run_gpu(args, world, rank, local):
     total_ms, _ = timed(False)
     prof_total_ms, prof = timed(True)
     clk = clocks.stop()
-    value = world * (na + nb) * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_value((na + nb) * args.steps, total_ms / 1e3, world)
     launches = sum(v[1] for v in prof.values())
 
     # end to end: host operands through gf2x_mul_host (pinned host buffers)
@@ -432,7 +447,7 @@ def run_gpu(args, world, rank, local):
         e2e_total = dist_max(sum(e2e_times), world)
         h2d = ((na + 63) // 64 + (nb + 63) // 64) * 8
         d2h = ((nc + 63) // 64) * 8
-        e2e = {"value": world * (na + nb) * args.steps / e2e_total / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_value((na + nb) * args.steps, e2e_total, world), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_total / args.steps}
         if not np.array_equal(cn, c.cpu().numpy().view(np.uint64)):
             raise RuntimeError("e2e product differs from the device-resident product")
