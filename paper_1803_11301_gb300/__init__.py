@@ -18,7 +18,7 @@ import os
 
 from .build import LIB as LIB_PATH
 
-__all__ = ["Context", "Gf2xError", "load_library", "transform_bits", "workspace_bytes",
+__all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_bits", "workspace_bytes",
            "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
            "ABI_FUNCTIONS", "STATUS"]
 
@@ -79,6 +79,17 @@ class Job(ctypes.Structure):
     """gf2x_job: one product of a batch (device pointers and bit lengths)."""
     _fields_ = [("a", ctypes.c_void_p), ("na_bits", ctypes.c_uint64), ("b", ctypes.c_void_p),
                 ("nb_bits", ctypes.c_uint64), ("c", ctypes.c_void_p)]
+
+
+class PreparedBatch:
+    """A job list marshalled for gf2x_mul_batch (see Context.prepare_batch)."""
+
+    def __init__(self, arr, count: int, workspace_bytes: int, outs, jobs):
+        self.arr = arr
+        self.count = count
+        self.workspace_bytes = workspace_bytes
+        self.outs = outs
+        self.jobs = jobs            # keeps the tensors the array points to alive
 
 
 class Gf2xError(RuntimeError):
@@ -303,8 +314,8 @@ class Context:
         """Launch a bounded wait that must run out; the status word then reads GF2X_ETIMEOUT."""
         _check(self._lib.gf2x_selftest_wait_timeout(self._h, self._stream(stream)), "gf2x_selftest_wait_timeout")
 
-    def mul_batch(self, jobs, workspace=None, stream=None):
-        """Run many products in one call.  jobs: list of (a, na, b, nb, c) with CUDA tensors."""
+    def prepare_batch(self, jobs) -> "PreparedBatch":
+        """Marshal a job list once (the gf2x_job array and its workspace size) for repeated calls."""
         arr = (Job * len(jobs))()
         for k, (a, na, b, nb, c) in enumerate(jobs):
             nc = product_bits(na, nb)
@@ -314,11 +325,17 @@ class Context:
         need = int(self._lib.gf2x_batch_workspace_bytes(arr, len(jobs)))
         if need == 0 and len(jobs):
             raise Gf2xError(1, "gf2x_batch_workspace_bytes")
+        return PreparedBatch(arr, len(jobs), need, [j[4] for j in jobs], list(jobs))
+
+    def mul_batch(self, jobs, workspace=None, stream=None):
+        """Run many products in one call.  jobs: a list of (a, na, b, nb, c) with CUDA tensors, or
+        a PreparedBatch (the same list marshalled once by prepare_batch; its tensors must stay alive)."""
+        pb = jobs if isinstance(jobs, PreparedBatch) else self.prepare_batch(jobs)
         if workspace is None:
-            workspace = self.workspace(need)
-        _check(self._lib.gf2x_mul_batch(self._h, arr, len(jobs), ctypes.c_void_p(workspace.data_ptr()),
+            workspace = self.workspace(pb.workspace_bytes)
+        _check(self._lib.gf2x_mul_batch(self._h, pb.arr, pb.count, ctypes.c_void_p(workspace.data_ptr()),
                                         workspace.numel(), self._stream(stream)), "gf2x_mul_batch")
-        return [j[4] for j in jobs]
+        return pb.outs
 
     def batch_workspace_bytes(self, jobs) -> int:
         arr = (Job * len(jobs))()

@@ -312,16 +312,22 @@ size_t bottom_smem(int bt, bool fused, int chunk)
 // 4.48 vs 4.08 ms at 16384 tiles).
 constexpr int kBottomThreadsSmall = 512, kBottomChunkSmall = 32;
 constexpr int kBottomThreadsLarge = 256, kBottomChunkLarge = 16;
+// A third shape for the tuner: 256 threads building 8 tables at a time (48 KiB
+// at 2^11-point tiles, 4 blocks per SM; more build rounds, more warps).
+constexpr int kBottomChunkLean = 8;
 
-// shape 1: the small-count shape, 0: the large-count one
+// shape 1: the small-count shape, 0: the large-count one, 2: the lean one
 cudaError_t launch_bottom_shape(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride,
                                 int shape, cudaStream_t st)
 {
     const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;
     const dim3 grid((unsigned)(1ull << (l - bt)), count);
-    if (shape)
+    if (shape == 1)
         k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall><<<grid, kBottomThreadsSmall,
             bottom_smem(bt, fused, kBottomChunkSmall), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+    else if (shape == 2)
+        k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean><<<grid, kBottomThreadsLarge,
+            bottom_smem(bt, fused, kBottomChunkLean), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
     else
         k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge><<<grid, kBottomThreadsLarge,
             bottom_smem(bt, fused, kBottomChunkLarge), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
@@ -337,8 +343,8 @@ void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int c
     const u64 tiles = 1ull << (l - bt);
     int shape = tiles * (u64)count < 4 * (u64)ctx->num_sms ? 1 : 0;
     if (scratch) {
-        static const int cands[2] = {1, 0};
-        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, (tune_bucket(tiles * (u64)count) << 2) | (u64)mode, cands, 2, shape,
+        static const int cands[3] = {1, 0, 2};
+        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, (tune_bucket(tiles * (u64)count) << 2) | (u64)mode, cands, 3, shape,
                             [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, st); },
                             st);
     }
@@ -400,6 +406,8 @@ void configure()
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkSmall));
     cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLarge));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLean));
     configured = true;
 }
 
