@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
     u64 *x = ((blockIdx.y % arrays) ? x1 : x0) + job * stride;
     const u64 first = (u64)blockIdx.x * per_block;
     const u64 group = first / chunks;
+    pdl_allow();
     build_tables(tabs, ntab, [&](int t) {
         const int lvl = 31 - __clz(t + 1);              // layer r = M-1-lvl holds 2^lvl tables
         const int r = M - 1 - lvl;
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
         return vb[l + 32 - (p + r)] ^ cantor(cvt, blk << 1);
     });
     const u64 rstride = 1ull << p;                      // distance between the rows of a column
+    pdl_wait();                                         // the twiddle tables need no earlier data
     for (int ch = 0; ch < per_block; ++ch) {
         const u64 chunk = first + ch;
         if (chunk / chunks != group) break;
@@ -265,6 +267,8 @@ __global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, 
     u64 *b = fused ? sm + T : nullptr;
     u64 *tabs = sm + (fused ? 2 : 1) * T;
     const u64 base = (u64)blockIdx.x << bt;
+    pdl_allow();
+    pdl_wait();
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
         a[k] = X[base + k];
         if (fused) b[k] = Y[base + k];
@@ -322,17 +326,21 @@ cudaError_t launch_bottom_shape(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, in
 {
     const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;
     const dim3 grid((unsigned)(1ull << (l - bt)), count);
+    cudaError_t e;
     if (shape == 1)
-        k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall><<<grid, kBottomThreadsSmall,
-            bottom_smem(bt, fused, kBottomChunkSmall), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall>, grid, dim3(kBottomThreadsSmall),
+                       bottom_smem(bt, fused, kBottomChunkSmall), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                       stride);
     else if (shape == 2)
-        k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean><<<grid, kBottomThreadsLarge,
-            bottom_smem(bt, fused, kBottomChunkLean), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean>, grid, dim3(kBottomThreadsLarge),
+                       bottom_smem(bt, fused, kBottomChunkLean), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                       stride);
     else
-        k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge><<<grid, kBottomThreadsLarge,
-            bottom_smem(bt, fused, kBottomChunkLarge), st>>>(X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode, stride);
+        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge>, grid, dim3(kBottomThreadsLarge),
+                       bottom_smem(bt, fused, kBottomChunkLarge), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                       stride);
     count_launch(ctx);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // The shape measured by the tuner on `scratch` (a free buffer laid out like X;
@@ -352,11 +360,12 @@ void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int c
 }
 
 template <int M, bool INV>
-void launch_top(dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
+void launch_top(bool pdl, dim3 grid, cudaStream_t st, u64 *x0, u64 *x1, int l, int p, u64 chunks, int per_block,
                 const u64 *cvt, const u64 *vb, int arrays, u64 stride)
 {
     size_t smem = (size_t)((1 << M) - 1) * kTab * sizeof(u64) + 128;
-    k_bfly_top<M, INV><<<grid, kThreads, smem, st>>>(x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride);
+    launch_pdl(pdl, k_bfly_top<M, INV>, grid, dim3(kThreads), smem, st, x0, x1, l, p, chunks, per_block, cvt, vb,
+               arrays, stride);
 }
 
 cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inverse, int count, u64 stride,
@@ -383,14 +392,14 @@ cudaError_t top_passes(gf2x_ctx *ctx, u64 *x0, u64 *x1, int l, int bt, bool inve
         dim3 grid((unsigned)(chunks * groups / per_block), (unsigned)(arrays * count));
         const u64 *cvt = ctx->d_cvt, *vb = ctx->d_cantor;
         switch (m * 2 + (inverse ? 1 : 0)) {
-        case 2: launch_top<1, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 3: launch_top<1, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 4: launch_top<2, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 5: launch_top<2, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 6: launch_top<3, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 7: launch_top<3, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        case 8: launch_top<4, false>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
-        default: launch_top<4, true>(grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 2: launch_top<1, false>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 3: launch_top<1, true>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 4: launch_top<2, false>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 5: launch_top<2, true>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 6: launch_top<3, false>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 7: launch_top<3, true>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        case 8: launch_top<4, false>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
+        default: launch_top<4, true>(ctx->pdl, grid, st, x0, x1, l, p, chunks, per_block, cvt, vb, arrays, stride); break;
         }
         count_launch(ctx);
     }

@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_allow();
     load_table_async(tab, enc);                   // in flight with the first tile's loads
+    pdl_wait();
     for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
         const u64 w0 = g * cols;
         __syncthreads();
@@ -93,9 +95,11 @@ __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 r
     __shared__ u64 tile[64 * kPad];
     const int cols = rw < kCols ? (int)rw : kCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_allow();
     load_table_async(tab, dec);
     copy_async_wait();
     __syncthreads();
+    pdl_wait();
     for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
         const u64 w0 = g * cols;
         for (int w = warp; w < cols; w += blockDim.x >> 5) {
@@ -289,7 +293,7 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
         int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
         if (rows > 64) rows = 64;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
-        k_encode<<<dim3((unsigned)grid, count), 256, 0, st>>>(novel, rw, rows, ctx->d_enc, f, groups, stride,
+        launch_pdl(ctx->pdl, k_encode, dim3((unsigned)grid, count), dim3(256), 0, st, novel, rw, rows, ctx->d_enc, f, groups, stride,
                                                                out_stride);
     }
     count_launch(ctx);
@@ -304,7 +308,7 @@ cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u6
         const u64 rw = 1ull << (l - 6);
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
-        k_decode<<<dim3((unsigned)grid, count), 256, 0, st>>>(h, rw, ctx->d_dec, novel, groups, stride);
+        launch_pdl(ctx->pdl, k_decode, dim3((unsigned)grid, count), dim3(256), 0, st, h, rw, ctx->d_dec, novel, groups, stride);
     }
     count_launch(ctx);
     return cudaGetLastError();

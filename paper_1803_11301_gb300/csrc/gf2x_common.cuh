@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <functional>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -96,6 +97,37 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
     }
 }
 
+// ------------------------------------------------ programmatic dependent launch
+// With `enable`, a kernel launched by launch_pdl may start while the kernel
+// before it in the stream is finishing.  Each of its blocks first lets its own
+// dependents launch (pdl_allow: they start once every block of this grid
+// runs), then does work that touches no data of earlier kernels (constant
+// tables, twiddle tables), then waits for the previous grid's completion and
+// memory (pdl_wait, a hardware dependency) before its first read or write of
+// the data.  Launched normally, both are no-ops.  Measured on GB300 it pays
+// for small products only (2^16 to 2^20-bit operands: 8-9% less time; at
+// 2^24 and 2^30 the early blocks compete with the previous kernel's last
+// wave: 1.5% more), so the products enable it by size (gf2x_ctx::pdl).
+__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool enable, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = enable ? attr : nullptr;
+    cfg.numAttrs = enable ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // One product of a batch as the device sees it (the job table lives in the
 // workspace).  nc = na + nb - 1 bits (0 if either is 0).
 struct JobDev {
@@ -151,6 +183,7 @@ struct gf2x_ctx {
     void *graphs;                       // CUDA graph cache of gf2x_mul, see api.cu
     void *batch_graphs;                 // CUDA graph cache of gf2x_mul_batch
     void *tuner;                        // measured launch-shape choices, see tune.cu
+    bool pdl;                           // launch_pdl overlaps kernels (set per product by size)
 };
 
 // Count one kernel launch against the current stage.
