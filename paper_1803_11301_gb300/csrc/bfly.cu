@@ -252,8 +252,88 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
     }
 }
 
+// The low kTableMin (= 4) layers in registers.  Layers 3..0 of the forward
+// transforms, the pointwise product and layers 0..3 of the inverse stay
+// inside aligned 16-point groups; 8 consecutive lanes hold a group, 2 points
+// each.  At layer i lane q (lane mod 8) holds points ins(q, i, 0) and
+// ins(q, i, 1) of its group (bit i inserted into q); going from the pairing of
+// layer i to that of layer j = i +- 1, each lane swaps one point with lane
+// q ^ 2^min(i, j): with b = bit min(i, j) of q it sends slot 1 - b and receives
+// into the same slot.  This replaces 9 shared-memory passes and barriers of
+// the tile by one load and one store.
+static_assert(kTableMin == 4, "the register phase covers layers 0..3");
+
+__device__ __forceinline__ int ins_bit(int q, int i, int s)
+{
+    return ((q >> i) << (i + 1)) | (s << i) | (q & ((1 << i) - 1));
+}
+
+__device__ __forceinline__ void pair_transition(u64 &x0, u64 &x1, int q, int lo)
+{
+    const int b = (q >> lo) & 1;
+    const u64 recv = __shfl_xor_sync(0xffffffffu, b ? x0 : x1, 1 << lo);
+    if (b) x0 = recv;
+    else x1 = recv;
+}
+
+// Runs on every thread of the block; the tile holds 2^bt >= 64 points, so each
+// warp's 4 groups are all inside the tile or all outside (warp-uniform loop).
+__device__ void low_layers_regs(u64 *a, const u64 *b, int bt, int l, u64 base, const u64 *__restrict__ cvt,
+                                const u64 *__restrict__ vb, bool fwd, bool fwd_b, bool fused, bool inv)
+{
+    const int T = 1 << bt;
+    const int q = threadIdx.x & 7;
+    u64 ctop[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ctop[i] = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+    for (int g0 = (threadIdx.x >> 3) * 16; g0 < T; g0 += (blockDim.x >> 3) * 16) {
+        const int first = fwd ? 3 : 0;
+        u64 x0 = a[g0 + ins_bit(q, first, 0)], x1 = a[g0 + ins_bit(q, first, 1)];
+        u64 y0 = 0, y1 = 0;
+        if (fused) {
+            y0 = b[g0 + ins_bit(q, first, 0)];
+            y1 = b[g0 + ins_bit(q, first, 1)];
+        }
+        if (fwd) {
+#pragma unroll
+            for (int i = 3; i >= 0; --i) {
+                const unsigned blk2 = (unsigned)((g0 + ins_bit(q, i, 0)) >> (i + 1)) << 1;   // 2 blk < 2^(bt-i)
+                const u64 c = ctop[i] ^ cvt[blk2 & 255] ^ cvt[256 + (blk2 >> 8)];
+                x0 ^= gf64_mul(c, x1);
+                x1 ^= x0;
+                if (fwd_b) {
+                    y0 ^= gf64_mul(c, y1);
+                    y1 ^= y0;
+                }
+                if (i > 0) {
+                    pair_transition(x0, x1, q, i - 1);
+                    if (fused) pair_transition(y0, y1, q, i - 1);
+                }
+            }
+        }
+        if (fused) {                                       // Alg. 5 line 7
+            x0 = gf64_mul(x0, y0);
+            x1 = gf64_mul(x1, y1);
+        }
+        int last = 0;
+        if (inv) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const unsigned blk2 = (unsigned)((g0 + ins_bit(q, i, 0)) >> (i + 1)) << 1;
+                const u64 c = ctop[i] ^ cvt[blk2 & 255] ^ cvt[256 + (blk2 >> 8)];
+                x1 ^= x0;
+                x0 ^= gf64_mul(c, x1);
+                if (i < 3) pair_transition(x0, x1, q, i);
+            }
+            last = 3;
+        }
+        a[g0 + ins_bit(q, last, 0)] = x0;
+        a[g0 + ins_bit(q, last, 1)] = x1;
+    }
+}
+
 template <int THREADS, int CHUNK>
-__global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
+__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt,
                                                           const u64 *__restrict__ vb, int mode, u64 stride)
 {
     extern __shared__ u64 smem_raw[];
@@ -274,6 +354,16 @@ __global__ void __launch_bounds__(THREADS) k_bfly_bottom(u64 *X, u64 *Y, int l, 
         if (fused) b[k] = Y[base + k];
     }
     __syncthreads();
+    if (bt >= 6) {                                      // layers 0..3 and the pointwise product in registers
+        for (int i = bt - 1; i >= kTableMin && mode != BOTTOM_INV; --i)
+            table_layer<CHUNK>(a, fwd_b ? b : nullptr, bt, i, l, base, cvt, vb, tabs, false);
+        low_layers_regs(a, b, bt, l, base, cvt, vb, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
+        __syncthreads();
+        for (int i = kTableMin; i < bt && mode != BOTTOM_FWD; ++i)
+            table_layer<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
+        for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
+        return;
+    }
     if (mode != BOTTOM_INV) {
         for (int i = bt - 1; i >= 0; --i) {
             if (i >= kTableMin) {
