@@ -139,7 +139,7 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
                                       void *stream);
 
 /* Reusing one operand.  When many products share the operand b, its forward
- * transform -- lines 4-6 of Alg. 5: BasisCvt, Encode, Butterfly, i.e. the
+ * transform -- the steps BasisCvt, Encode, Butterfly of Alg. 5, i.e. the
  * values B(alpha + u_k) of Eq. 8 at the n_p points of Sigma -- can be
  * computed once and passed to every product, which then skips them.
  *
@@ -160,7 +160,7 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
  *   read.  Other arguments, sizes and errors as for gf2x_mul; c must not
  *   overlap bhat.  Both calls replay from a captured CUDA graph from the
  *   second identical call on, like gf2x_mul.  The paper has no separate
- *   entry point for this; it is lines 1-10 of Alg. 5 with lines 4-6 done
+ *   entry point for this; it is Alg. 5 with b's forward steps done
  *   ahead of time. */
 GF2X_API size_t gf2x_transform_bytes(uint64_t n_bits);
 GF2X_API gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb_bits, uint64_t n_bits,
@@ -278,7 +278,7 @@ GF2X_API gf2x_status gf2x_butterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits,
 /* iButterfly: the inverse of gf2x_butterfly, in place. */
 GF2X_API gf2x_status gf2x_ibutterfly(gf2x_ctx *ctx, uint64_t *f, uint64_t n_bits, void *stream);
 
-/* Pointwise product in GF(2^64) (Alg. 5 line 7): c[i] = a[i] * b[i],
+/* Pointwise product in GF(2^64) (pointwise step of Alg. 5): c[i] = a[i] * b[i],
  * i < count.  c may alias a or b. */
 GF2X_API gf2x_status gf2x_pointwise(gf2x_ctx *ctx, const uint64_t *a, const uint64_t *b,
                            uint64_t *c, uint64_t count, void *stream);

@@ -13,7 +13,7 @@ Conventions
   l = l_n - 6, n_p = 2^l and alpha = v_{l+32} (Eq. 6).
 
 Readings of the paper used here (the paper is silent or garbled there):
-* Alg. 1 line 4/5 writes X_{(m-1) 2^k}; with i = 2^k and s_i = X_{2^i} the
+* Alg. 1 writes the block multiplier as X_{(m-1) 2^k}; with i = 2^k and s_i = X_{2^i} the
   block multiplier is X_{j 2^i}.  That is what the recursion below produces.
 * Eq. 9 / Sec. 3.3 list the Encode multipliers as v_{31}, ..., v_{26}
   (s_{l+1} .. s_{l+6} at v_{l+32}).  The first l_m truncated layers of
@@ -100,7 +100,7 @@ def _taylor(f: list[int], tau: int) -> list[list[int]]:
     """Digits h_j (each tau coefficients) with f = sum_j h_j * s^j, s = y^tau + y.
 
     Recursive division by s^(2^k) = y^(tau 2^k) + y^(2^k) (char. 2), the
-    largest power of s of degree L/2 (Alg. 1 line 3).
+    largest power of s of degree L/2 (Alg. 1).
     """
     L = len(f)
     if L <= tau:
@@ -367,7 +367,7 @@ def eval_at_sigma(A: int, n: int) -> np.ndarray:
 
 # ------------------------------------------------------ FP_Polymul (Alg. 5)
 def forward(a: int, na: int, n: int, tw: Twiddles) -> np.ndarray:
-    """Lines 1-3 of Alg. 5 for one operand: BasisCvt, Encode, Butterfly at alpha."""
+    """The forward steps of Alg. 5 for one operand: BasisCvt, Encode, Butterfly at alpha."""
     A_novel = basis_cvt(a & ((1 << na) - 1), n)
     return butterfly(encode(A_novel, n), tw)
 
@@ -381,10 +381,10 @@ def fp_polymul(a: int, na: int, b: int, nb: int) -> int:
     tw = Twiddles(l)
     ahat = forward(a, na, n, tw)
     bhat = forward(b, nb, n, tw)
-    chat = F.gf_mul_arr(ahat, bhat)                  # line 7
-    h = ibutterfly(chat, tw)                          # line 8
-    C_novel = decode(h, n)                            # line 9
-    return ibasis_cvt(C_novel, n)                     # line 10
+    chat = F.gf_mul_arr(ahat, bhat)                  # pointwise
+    h = ibutterfly(chat, tw)                          # iButterfly
+    C_novel = decode(h, n)                            # Decode
+    return ibasis_cvt(C_novel, n)                     # iBasisCvt
 
 
 # ------------------------------------------------ novelpoly evaluation (Def.)

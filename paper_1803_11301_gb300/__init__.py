@@ -248,7 +248,7 @@ class Context:
         return int(fn(self._h, na, nb))
 
     def forward_transform(self, b, nb: int, n: int, out=None, workspace=None, stream=None):
-        """The transform of b (lines 4-6 of Alg. 5) at transform length n, for reuse."""
+        """The transform of b (the BasisCvt, Encode and Butterfly steps of Alg. 5) at transform length n, for reuse."""
         if out is None:
             out = self.empty_words(n // 64)
         need = 3 * ((n // 8 + 255) // 256 * 256) + 256

@@ -5,11 +5,11 @@
 // FP_Polymul (Alg. 5) on one stream, three workspace buffers X, Y, T of n/64
 // words each:
 //   T <- a (masked, zero-padded to n bits); BasisCvt(T, L_a); X <- Encode(T)
-//   T <- b ...;                                       Y <- Encode(T)   (lines 1-2, 4-5)
-//   top Butterfly layers of X and Y                                    (lines 3, 6)
+//   T <- b ...;                                       Y <- Encode(T)   (BasisCvt, Encode)
+//   top Butterfly layers of X and Y                                    (Butterfly)
 //   one kernel per 2^11-point tile: low layers of both Butterflies,
-//     X <- X * Y, low layers of the iButterfly                        (lines 3, 6, 7, 8)
-//   top iButterfly layers of X; T <- Decode(X); iBasisCvt(T, n); c <- T (lines 8-10)
+//     X <- X * Y, low layers of the iButterfly                        (Butterfly, pointwise, iButterfly)
+//   top iButterfly layers of X; T <- Decode(X); iBasisCvt(T, n); c <- T (the inverse steps)
 // BasisCvt runs on L_a = max(64, next_pow2(na)) bits: the novelpoly basis
 // is triangular (deg X_k = k), so the coefficients at k >= L_a are zero.
 #include <algorithm>
@@ -400,7 +400,8 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
         s = forward(ctx, r, 1, r.Y, st);
         if (s != GF2X_OK) return s;
     }
-    // lines 3 and 6 (top layers), then 3, 6, 7, 8 on the low layers in one kernel, then 8 (top layers)
+    // both Butterflies (top layers), then both Butterflies, the pointwise product and the iButterfly on
+    // the low layers in one kernel, then the iButterfly's top layers
     {
         StageScope g(ctx, STAGE_BUTTERFLY, st);
         TRY(gf2x::butterfly_top_pair(ctx, r.X, r.Y, l, r.count, r.stride, st, bt));
@@ -413,7 +414,7 @@ gf2x_status run_class(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
     return inverse_tail(ctx, r, st, bt);
 }
 
-// Lines 4-6 of Alg. 5 on their own: bhat <- Butterfly(Encode(BasisCvt(b)))
+// The forward steps of Alg. 5 for b on their own: bhat <- Butterfly(Encode(BasisCvt(b)))
 // at transform length n, for reuse by products with that n.  Workspace as for
 // a product with transform length n: X is BasisCvt's scratch, T the bit array.
 gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n, u64 *bhat, void *ws,
@@ -431,7 +432,7 @@ gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n,
 }
 
 // c = a * b with b given as its forward transform bhat (at n = transform
-// length of na x nb): lines 1-3 for a, 7 with bhat, 8-10.
+// length of na x nb): the forward steps for a, the pointwise product with bhat, the inverse steps.
 gf2x_status mul_transformed_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *bhat, u64 nb, u64 *c, void *ws,
                                    cudaStream_t st)
 {

@@ -17,8 +17,8 @@
 // memory, one layer after the other.  Layers i >= kTableMin (twiddle shared by
 // 2^i butterflies per array) use tables, built 32 at a time; layers
 // 0..kTableMin-1 multiply with the integer form.  In the fused mode the tile holds the matching tiles of both
-// transforms: forward A, forward B, pointwise product, inverse (Alg. 5 lines
-// 3, 6, 7, 8 for the low layers) in one pass over HBM.
+// transforms: forward A, forward B, pointwise product, inverse (the Butterfly,
+// pointwise and iButterfly steps of Alg. 5 on the low layers) in one pass over HBM.
 //
 // Multiplication table (method of four Russians, Sec. 4.5): for a fixed c,
 // tab[w][e] = c * (e x^(4w)) for the 16 four-bit windows w and e < 16, so
@@ -311,7 +311,7 @@ __device__ void low_layers_regs(u64 *a, const u64 *b, int bt, int l, u64 base, c
                 }
             }
         }
-        if (fused) {                                       // Alg. 5 line 7
+        if (fused) {                                       // pointwise step of Alg. 5
             x0 = gf64_mul(x0, y0);
             x1 = gf64_mul(x1, y1);
         }
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom
         }
     }
     if (fused) {
-        for (int k = threadIdx.x; k < T; k += blockDim.x) a[k] = gf64_mul(a[k], b[k]);   // Alg. 5 line 7
+        for (int k = threadIdx.x; k < T; k += blockDim.x) a[k] = gf64_mul(a[k], b[k]);   // pointwise step of Alg. 5
         __syncthreads();
     }
     if (mode != BOTTOM_FWD) {

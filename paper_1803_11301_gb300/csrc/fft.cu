@@ -1,4 +1,4 @@
-// Encode / Decode (Alg. 4), the pointwise product (Alg. 5 line 7) and the
+// Encode / Decode (Alg. 4), the pointwise product of Alg. 5 and the
 // bit-array load/store around them.
 #include "gf2x_common.cuh"
 
@@ -24,7 +24,7 @@ __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_
 // n_p = 2^l >= 64.  Row j of the novelpoly bit array is bits [j n_p, (j+1) n_p),
 // i.e. RW = n_p/64 words.  For the 64 points i in word column w, the 64 words
 // (row j, column w) form a 64x64 bit matrix whose transpose gives, per i, the
-// vector (a_{j n_p + i})_j; f_i = that vector times R (Alg. 4 lines 3-4).
+// vector (a_{j n_p + i})_j; f_i = that vector times R (Alg. 4).
 //
 // A block stages 64 rows x 32 word columns in shared memory (coalesced row
 // reads); each warp transposes one column's 64x64 bit matrix with shuffles

@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle -- needs a GPU.
 
 Integer work, so the bar is bit-exact everywhere.  Stage by stage (Alg. 1,
-4, 2, Alg. 5 line 7) against ``oracle.stages``; end to end (Alg. 5) against
+4, 2, the pointwise step of Alg. 5) against ``oracle.stages``; end to end (Alg. 5) against
 the Karatsuba oracle where it finishes and against the modular checker at
 2^30-bit operands; the forward transform sampled against evaluation at the
 partition (Eq. 8) at full size.
@@ -351,7 +351,7 @@ def test_serving_results_same_alone_and_in_the_mix(ctx):
 # ------------------------------------------------------------ reused operand
 @pytest.mark.parametrize("na,nb", [(100, 5000), (1 << 16, 1 << 16), (70001, 3333), (1 << 20, 1 << 18), (64, 64)])
 def test_reused_operand_transform(ctx, na, nb):
-    # lines 4-6 of Alg. 5 once for b (gf2x_forward_transform), then products
+    # the forward steps of Alg. 5 once for b (gf2x_forward_transform), then products
     # with several a of the same transform length (gf2x_mul_transformed)
     from paper_1803_11301_gb300 import transform_bits
     b = synth.operand(synth.config_seed(9, nb), nb)
