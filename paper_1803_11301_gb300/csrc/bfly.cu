@@ -252,6 +252,86 @@ __device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, cons
     }
 }
 
+// Butterflies of layer i for the blocks j0 .. j0 + nt - 1 of the tile(s),
+// block j's table at slot slot0 + j - j0 of tabs; on A and, if given, B.
+__device__ __forceinline__ void table_butterflies(u64 *a, u64 *b, int i, int j0, int nt, int slot0, const u64 *tabs,
+                                                  bool inverse)
+{
+    const int span = 1 << i;
+    for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
+        const int blk = j0 + (t >> i), jj = t & (span - 1);
+        const int s0 = (blk << (i + 1)) + jj;
+        const unsigned tb = smem_addr(tabs) + (unsigned)((slot0 + blk - j0) * kTab * 8);
+        u64 x0 = a[s0], x1 = a[s0 + span];
+        if (!inverse) {
+            x0 ^= mul_tab(tb, x1);
+            x1 ^= x0;
+        } else {
+            x1 ^= x0;
+            x0 ^= mul_tab(tb, x1);
+        }
+        a[s0] = x0;
+        a[s0 + span] = x1;
+        if (b) {
+            u64 y0 = b[s0], y1 = b[s0 + span];
+            y0 ^= mul_tab(tb, y1);
+            y1 ^= y0;
+            b[s0] = y0;
+            b[s0 + span] = y1;
+        }
+    }
+}
+
+// The table layers bt-1 .. kTableMin of a tile in the order of the pass
+// (forward top down, inverse bottom up), twiddle tables packed.  The layers
+// i >= bt - log2(CHUNK) have 2^(bt-i) - 1 tables together (layer i's block j
+// at slot 2^(bt-1-i) - 1 + j), built in one round by the whole block; each
+// lower layer has 2^(bt-1-i) >= CHUNK tables, built CHUNK at a time.  The
+// inverse takes the groups in reverse order, so its first group is the last
+// one of the forward pass: with `kept` those tables are still in tabs and are
+// not built again.  ctops[i] = v_{l+32-i} + Cantor((tile base) >> i), and the
+// block j of layer i adds Cantor(2j), 2j < 2^(bt-i) <= 2^11 (two byte windows).
+template <int CHUNK>
+__device__ void table_layers(u64 *a, u64 *b, int bt, const u64 *__restrict__ cvt, const u64 *ctops, u64 *tabs,
+                             bool inverse, bool kept)
+{
+    static_assert(CHUNK == 8 || CHUNK == 16 || CHUNK == 32, "chunk of 8, 16 or 32 tables");
+    constexpr int kLogChunk = CHUNK == 8 ? 3 : CHUNK == 16 ? 4 : 5;
+    const int lo_top = bt - kLogChunk > kTableMin ? bt - kLogChunk : kTableMin;
+    auto twid = [&](int i, int j) {
+        const unsigned j2 = (unsigned)j << 1;
+        return ctops[i] ^ cvt[j2 & 255] ^ cvt[256 + (j2 >> 8)];
+    };
+    auto packed = [&](bool build) {
+        if (build)
+            build_tables(tabs, (1 << (bt - lo_top)) - 1, [&](int t) {
+                const int r = 31 - __clz(t + 1);            // slot t: block t + 1 - 2^r of layer bt-1-r
+                return twid(bt - 1 - r, t + 1 - (1 << r));
+            });
+        for (int k = 0; k < bt - lo_top; ++k) {
+            const int i = inverse ? lo_top + k : bt - 1 - k;
+            table_butterflies(a, b, i, 0, 1 << (bt - 1 - i), (1 << (bt - 1 - i)) - 1, tabs, inverse);
+            __syncthreads();
+        }
+    };
+    auto chunked = [&](int i, bool first_kept) {
+        const int nc = (1 << (bt - 1 - i)) / CHUNK;
+        for (int c = 0; c < nc; ++c) {
+            const int j0 = (inverse ? nc - 1 - c : c) * CHUNK;
+            if (!(first_kept && c == 0)) build_tables(tabs, CHUNK, [&](int t) { return twid(i, j0 + t); });
+            table_butterflies(a, b, i, j0, CHUNK, 0, tabs, inverse);
+            __syncthreads();
+        }
+    };
+    if (!inverse) {
+        packed(true);
+        for (int i = lo_top - 1; i >= kTableMin; --i) chunked(i, false);
+    } else {
+        for (int i = kTableMin; i < lo_top; ++i) chunked(i, kept && i == kTableMin);
+        packed(!(kept && lo_top == kTableMin));
+    }
+}
+
 // The low kTableMin (= 4) layers in registers.  Layers 3..0 of the forward
 // transforms, the pointwise product and layers 0..3 of the inverse stay
 // inside aligned 16-point groups; 8 consecutive lanes hold a group, 2 points
@@ -278,14 +358,14 @@ __device__ __forceinline__ void pair_transition(u64 &x0, u64 &x1, int q, int lo)
 
 // Runs on every thread of the block; the tile holds 2^bt >= 64 points, so each
 // warp's 4 groups are all inside the tile or all outside (warp-uniform loop).
-__device__ void low_layers_regs(u64 *a, const u64 *b, int bt, int l, u64 base, const u64 *__restrict__ cvt,
-                                const u64 *__restrict__ vb, bool fwd, bool fwd_b, bool fused, bool inv)
+__device__ void low_layers_regs(u64 *a, const u64 *b, int bt, const u64 *__restrict__ cvt, const u64 *ctops, bool fwd,
+                                bool fwd_b, bool fused, bool inv)
 {
     const int T = 1 << bt;
     const int q = threadIdx.x & 7;
     u64 ctop[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) ctop[i] = vb[l + 32 - i] ^ cantor(cvt, base >> i);
+    for (int i = 0; i < 4; ++i) ctop[i] = ctops[i];
     for (int g0 = (threadIdx.x >> 3) * 16; g0 < T; g0 += (blockDim.x >> 3) * 16) {
         const int first = fwd ? 3 : 0;
         u64 x0 = a[g0 + ins_bit(q, first, 0)], x1 = a[g0 + ins_bit(q, first, 1)];
@@ -353,14 +433,14 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom
         a[k] = X[base + k];
         if (fused) b[k] = Y[base + k];
     }
+    u64 *ctops = tabs + CHUNK * kTab;                   // v_{l+32-i} + Cantor(base >> i), i < bt
+    if (threadIdx.x < bt) ctops[threadIdx.x] = vb[l + 32 - threadIdx.x] ^ cantor(cvt, base >> threadIdx.x);
     __syncthreads();
     if (bt >= 6) {                                      // layers 0..3 and the pointwise product in registers
-        for (int i = bt - 1; i >= kTableMin && mode != BOTTOM_INV; --i)
-            table_layer<CHUNK>(a, fwd_b ? b : nullptr, bt, i, l, base, cvt, vb, tabs, false);
-        low_layers_regs(a, b, bt, l, base, cvt, vb, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
+        if (mode != BOTTOM_INV) table_layers<CHUNK>(a, fwd_b ? b : nullptr, bt, cvt, ctops, tabs, false, false);
+        low_layers_regs(a, b, bt, cvt, ctops, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
         __syncthreads();
-        for (int i = kTableMin; i < bt && mode != BOTTOM_FWD; ++i)
-            table_layer<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
+        if (mode != BOTTOM_FWD) table_layers<CHUNK>(a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);
         for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
         return;
     }
@@ -396,7 +476,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom
 
 size_t bottom_smem(int bt, bool fused, int chunk)
 {
-    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)chunk * kTab) * sizeof(u64) + 128;
+    return ((fused ? 2 : 1) * (size_t)(1 << bt) + (size_t)chunk * kTab + 16) * sizeof(u64) + 128;
 }
 
 // Bottom kernel shapes (threads per block, tables built at a time): with few
