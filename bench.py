@@ -82,8 +82,10 @@ BOTTOM_LAYERS_128 = 10
 # profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/launch_list_gf2x_mul_m128_2e24x2e24.md).
 # An entry is removed when its kernel changes; a missing entry reports null.
 TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers)
-    ("bottom_fused", 1 << 24, 1 << 24, 128, 9): 8467968 + 0,
-    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): 537103616 + 225052672,
+    ("bottom_fused", 1 << 24, 1 << 24, 64, 9): 8468224 + 0,
+    ("bottom_fused", 1 << 24, 1 << 24, 128, 9): 8488192 + 0,
+    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): 538430976 + 225118720,
+    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): 537023232 + 225316096,
 }
 
 

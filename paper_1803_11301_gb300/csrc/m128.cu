@@ -417,42 +417,84 @@ __device__ __forceinline__ void tile_layer128(u64 *a, int bt, int i, g128 ctop, 
     }
 }
 
-// Layer i >= kTableMin128 on the tile(s): the 2^(bt-1-i) twiddles
-// c_j = v_{l+64-i} + Cantor((base >> i) + 2j) get tables CHUNK at a time;
-// each chunk's butterflies run on a and, if given, b.
-template <int CHUNK>
-__device__ void table_layer128(u64 *a, u64 *b, int bt, int i, int l, u64 base, const u64 *__restrict__ cvt,
-                               const u64 *__restrict__ vb, u64 *tabs, bool inverse)
+// Butterflies of layer i for the blocks j0 .. j0 + nt - 1 of the tile(s),
+// block j's table at slot slot0 + j - j0 of tabs; on a and, if given, b.
+__device__ __forceinline__ void table_butterflies128(u64 *a, u64 *b, int i, int j0, int nt, int slot0, const u64 *tabs,
+                                                     bool inverse)
 {
-    const int ntot = 1 << (bt - 1 - i);
     const int span = 1 << i;
-    const g128 vtop = ld128(vb + 2 * (l + 64 - i));
-    for (int j0 = 0; j0 < ntot; j0 += CHUNK) {
-        const int nt = ntot - j0 < CHUNK ? ntot - j0 : CHUNK;
-        build_tables128(tabs, nt, [&](int t) { return gx(vtop, cantor128(cvt, (base >> i) + ((u64)(j0 + t) << 1))); });
-        for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
-            const int blk = j0 + (t >> i), jj = t & (span - 1);
-            const int s0 = (blk << (i + 1)) + jj;
-            const unsigned tb = smem_addr128(tabs) + (unsigned)((blk - j0) * kTab128 * 8);
-            g128 x0 = ld128(a + 2 * s0), x1 = ld128(a + 2 * (s0 + span));
-            if (!inverse) {
-                x0 = gx(x0, mul_tab128(tb, x1));
-                x1 = gx(x1, x0);
-            } else {
-                x1 = gx(x1, x0);
-                x0 = gx(x0, mul_tab128(tb, x1));
-            }
-            st128(a + 2 * s0, x0);
-            st128(a + 2 * (s0 + span), x1);
-            if (b) {
-                g128 y0 = ld128(b + 2 * s0), y1 = ld128(b + 2 * (s0 + span));
-                y0 = gx(y0, mul_tab128(tb, y1));
-                y1 = gx(y1, y0);
-                st128(b + 2 * s0, y0);
-                st128(b + 2 * (s0 + span), y1);
-            }
+    for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
+        const int blk = j0 + (t >> i), jj = t & (span - 1);
+        const int s0 = (blk << (i + 1)) + jj;
+        const unsigned tb = smem_addr128(tabs) + (unsigned)((slot0 + blk - j0) * kTab128 * 8);
+        g128 x0 = ld128(a + 2 * s0), x1 = ld128(a + 2 * (s0 + span));
+        if (!inverse) {
+            x0 = gx(x0, mul_tab128(tb, x1));
+            x1 = gx(x1, x0);
+        } else {
+            x1 = gx(x1, x0);
+            x0 = gx(x0, mul_tab128(tb, x1));
         }
-        __syncthreads();
+        st128(a + 2 * s0, x0);
+        st128(a + 2 * (s0 + span), x1);
+        if (b) {
+            g128 y0 = ld128(b + 2 * s0), y1 = ld128(b + 2 * (s0 + span));
+            y0 = gx(y0, mul_tab128(tb, y1));
+            y1 = gx(y1, y0);
+            st128(b + 2 * s0, y0);
+            st128(b + 2 * (s0 + span), y1);
+        }
+    }
+}
+
+// The table layers bt-1 .. kTableMin128 of a tile in the order of the pass
+// (forward top down, inverse bottom up), twiddle tables packed as in the
+// m = 64 bottom kernel: the layers i >= bt - log2(CHUNK) have 2^(bt-i) - 1
+// tables together (layer i's block j at slot 2^(bt-1-i) - 1 + j), built in
+// one round; each lower layer has 2^(bt-1-i) >= CHUNK tables, built CHUNK at
+// a time.  The inverse takes the groups in reverse order, so its first group
+// is the forward pass's last one: with `kept` those tables are still in tabs.
+// ctops[i] = v_{l+64-i} + Cantor((tile base) >> i) (two words); block j of
+// layer i adds Cantor(2j), 2j < 2^(bt-i) <= 2^10 (two byte windows).
+template <int CHUNK>
+__device__ void table_layers128(u64 *a, u64 *b, int bt, const u64 *__restrict__ cvt, const u64 *ctops, u64 *tabs,
+                                bool inverse, bool kept)
+{
+    static_assert(CHUNK == 4 || CHUNK == 8, "chunk of 4 or 8 tables");
+    constexpr int kLogChunk = CHUNK == 4 ? 2 : 3;
+    if (bt <= kTableMin128) return;
+    const int lo_top = bt - kLogChunk > kTableMin128 ? bt - kLogChunk : kTableMin128;
+    auto twid = [&](int i, int j) {
+        const unsigned j2 = (unsigned)j << 1;
+        return gx(ld128(ctops + 2 * i), gx(ld128(cvt + 2 * (j2 & 255)), ld128(cvt + 2 * (256 + (j2 >> 8)))));
+    };
+    auto packed = [&](bool build) {
+        if (build)
+            build_tables128(tabs, (1 << (bt - lo_top)) - 1, [&](int t) {
+                const int r = 31 - __clz(t + 1);            // slot t: block t + 1 - 2^r of layer bt-1-r
+                return twid(bt - 1 - r, t + 1 - (1 << r));
+            });
+        for (int k = 0; k < bt - lo_top; ++k) {
+            const int i = inverse ? lo_top + k : bt - 1 - k;
+            table_butterflies128(a, b, i, 0, 1 << (bt - 1 - i), (1 << (bt - 1 - i)) - 1, tabs, inverse);
+            __syncthreads();
+        }
+    };
+    auto chunked = [&](int i, bool first_kept) {
+        const int nc = (1 << (bt - 1 - i)) / CHUNK;
+        for (int c = 0; c < nc; ++c) {
+            const int j0 = (inverse ? nc - 1 - c : c) * CHUNK;
+            if (!(first_kept && c == 0)) build_tables128(tabs, CHUNK, [&](int t) { return twid(i, j0 + t); });
+            table_butterflies128(a, b, i, j0, CHUNK, 0, tabs, inverse);
+            __syncthreads();
+        }
+    };
+    if (!inverse) {
+        packed(true);
+        for (int i = lo_top - 1; i >= kTableMin128; --i) chunked(i, false);
+    } else {
+        for (int i = kTableMin128; i < lo_top; ++i) chunked(i, kept && i == kTableMin128);
+        packed(!(kept && lo_top == kTableMin128));
     }
 }
 
@@ -462,7 +504,7 @@ __host__ __device__ __forceinline__ int tile_words128(int bt) { return (2 << bt)
 
 // One tile of 2^bt points per block: the low layers of the forward transform
 // (of X, and of Y in the fused mode), then in the fused mode the pointwise
-// product X * Y (Alg. 5 line 7), then the low layers of the inverse.
+// product X * Y (pointwise step of Alg. 5), then the low layers of the inverse.
 template <int CHUNK>
 __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u64 *Y, int l, int bt,
                                                                 const u64 *__restrict__ cvt, const u64 *__restrict__ vb,
@@ -482,17 +524,18 @@ __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u6
         st128(a + 2 * k, ld128(X + 2 * (base + k)));
         if (fused) st128(b + 2 * k, ld128(Y + 2 * (base + k)));
     }
+    u64 *ctops = tabs + CHUNK * kTab128;                // v_{l+64-i} + Cantor(base >> i), i < bt
+    if (threadIdx.x < bt)
+        st128(ctops + 2 * threadIdx.x, gx(ld128(vb + 2 * (l + 64 - threadIdx.x)), cantor128(cvt, base >> threadIdx.x)));
     __syncthreads();
+    const int low = bt < kTableMin128 ? bt : kTableMin128;   // layers below `low` multiply in integer form
     if (mode != B128_INV) {
-        for (int i = bt - 1; i >= 0; --i) {
-            if (i >= kTableMin128) {
-                table_layer128<CHUNK>(a, b, bt, i, l, base, cvt, vb, tabs, false);
-            } else {
-                const g128 ctop = gx(ld128(vb + 2 * (l + 64 - i)), cantor128(cvt, base >> i));
-                tile_layer128(a, bt, i, ctop, cvt, false);
-                if (fused) tile_layer128(b, bt, i, ctop, cvt, false);
-                __syncthreads();
-            }
+        table_layers128<CHUNK>(a, b, bt, cvt, ctops, tabs, false, false);
+        for (int i = low - 1; i >= 0; --i) {
+            const g128 ctop = ld128(ctops + 2 * i);
+            tile_layer128(a, bt, i, ctop, cvt, false);
+            if (fused) tile_layer128(b, bt, i, ctop, cvt, false);
+            __syncthreads();
         }
     }
     if (fused) {
@@ -500,22 +543,18 @@ __global__ void __launch_bounds__(kThreads128) k128_bfly_bottom(u64 *X, const u6
         __syncthreads();
     }
     if (mode != B128_FWD) {
-        for (int i = 0; i < bt; ++i) {
-            if (i >= kTableMin128) {
-                table_layer128<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
-            } else {
-                const g128 ctop = gx(ld128(vb + 2 * (l + 64 - i)), cantor128(cvt, base >> i));
-                tile_layer128(a, bt, i, ctop, cvt, true);
-                __syncthreads();
-            }
+        for (int i = 0; i < low; ++i) {
+            tile_layer128(a, bt, i, ld128(ctops + 2 * i), cvt, true);
+            __syncthreads();
         }
+        table_layers128<CHUNK>(a, nullptr, bt, cvt, ctops, tabs, true, mode != B128_INV);
     }
     for (int k = threadIdx.x; k < T; k += blockDim.x) st128(X + 2 * (base + k), ld128(a + 2 * k));
 }
 
 size_t bottom_smem128(int bt, bool fused, int chunk)
 {
-    return ((fused ? 2 : 1) * (size_t)tile_words128(bt) + (size_t)chunk * kTab128) * sizeof(u64) + 128;
+    return ((fused ? 2 : 1) * (size_t)tile_words128(bt) + (size_t)chunk * kTab128 + 32) * sizeof(u64) + 128;
 }
 
 size_t top_smem128(int m) { return (size_t)((1 << m) - 1) * kTab128 * sizeof(u64) + 128; }
