@@ -216,6 +216,31 @@ GF2X_API gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream);
  * GF2X_TUNE=0 in the environment at context creation never measures. */
 GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
 
+/* Pinning one launch choice, for reproducible launch shapes and for testing
+ * every variant.  Wherever `choice` is one of the knob's candidates for a call
+ * it is used without measuring; elsewhere (a depth deeper than the transform,
+ * say) the tuner decides as before.  choice = -1 releases the knob.  Graphs
+ * captured before the call are not replayed again (the next calls capture
+ * anew).  Knobs and their candidates, all computing the same result:
+ *   GF2X_KNOB_UNIT16_R           words per thread of the 2^16-bit BasisCvt kernel: 8, 16, 32
+ *   GF2X_KNOB_BOTTOM_SHAPE       fused bottom kernel: 0 (256 threads, 16-table chunks),
+ *                                1 (512 threads, 32), 2 (256 threads, 8)
+ *   GF2X_KNOB_WINDOW_DEPTH       Taylor layers in BasisCvt's window kernel: 6, 7, 8
+ *   GF2X_KNOB_M128_BOTTOM_CHUNK  GF(2^128) bottom kernel tables per chunk: 4, 8
+ *   GF2X_KNOB_BOTTOM_DEPTH       Butterfly layers in the bottom kernel: 8 .. 11
+ *   GF2X_KNOB_M128_BOTTOM_DEPTH  the same for GF(2^128) points: 8 .. 10
+ * GF2X_EINVAL for a NULL context, an unknown knob or choice < -1.  Not
+ * thread-safe against calls running on the same context. */
+enum {
+    GF2X_KNOB_UNIT16_R = 1,
+    GF2X_KNOB_BOTTOM_SHAPE = 2,
+    GF2X_KNOB_WINDOW_DEPTH = 3,
+    GF2X_KNOB_M128_BOTTOM_CHUNK = 4,
+    GF2X_KNOB_BOTTOM_DEPTH = 5,
+    GF2X_KNOB_M128_BOTTOM_DEPTH = 6
+};
+GF2X_API gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice);
+
 /* Butterfly layers (Alg. 2) that gf2x_mul runs in its fused low-layer kernel
  * for an na x nb product, the rest running as passes over HBM: the depth the
  * context's tuner measured at the first product of this transform length, or

@@ -20,7 +20,8 @@ from .build import LIB as LIB_PATH
 
 __all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_bits", "workspace_bytes",
            "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
-           "ABI_FUNCTIONS", "STATUS"]
+           "ABI_FUNCTIONS", "STATUS", "KNOB_UNIT16_R", "KNOB_BOTTOM_SHAPE", "KNOB_WINDOW_DEPTH",
+           "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH"]
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
           5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE"}
@@ -57,6 +58,7 @@ ABI_FUNCTIONS = {
     "gf2x_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
     "gf2x_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
     "gf2x_tune_freeze": (_ST, [_P, ctypes.c_int]),
+    "gf2x_tune_pin": (_ST, [_P, ctypes.c_int, ctypes.c_int]),
     "gf2x_m128_transform_bits": (_U64, [_U64, _U64]),
     "gf2x_m128_bottom_layers": (ctypes.c_int, [_P, _U64, _U64]),
     "gf2x_m128_workspace_bytes": (_SZ, [_U64, _U64]),
@@ -73,6 +75,16 @@ ABI_FUNCTIONS = {
 }
 
 _lib = None
+
+
+# Launch knobs of Context.tune_pin (the GF2X_KNOB_* constants of include/gf2x.h)
+# and their candidates.
+KNOB_UNIT16_R = 1              # 8, 16, 32
+KNOB_BOTTOM_SHAPE = 2          # 0, 1, 2
+KNOB_WINDOW_DEPTH = 3          # 6, 7, 8
+KNOB_M128_BOTTOM_CHUNK = 4     # 4, 8
+KNOB_BOTTOM_DEPTH = 5          # 8 .. 11
+KNOB_M128_BOTTOM_DEPTH = 6     # 8 .. 10
 
 
 class Job(ctypes.Structure):
@@ -241,6 +253,10 @@ class Context:
     def tune_freeze(self, frozen: bool = True):
         """Stop (or resume) measuring launch shapes on first use; stored choices stay."""
         _check(self._lib.gf2x_tune_freeze(self._h, 1 if frozen else 0), "gf2x_tune_freeze")
+
+    def tune_pin(self, knob: int, choice: int):
+        """Use `choice` for launch knob `knob` (KNOB_*) wherever it is a candidate; -1 releases it."""
+        _check(self._lib.gf2x_tune_pin(self._h, int(knob), int(choice)), "gf2x_tune_pin")
 
     def bottom_layers(self, na: int, nb: int, field: int = 64) -> int:
         """Butterfly layers of an na x nb product done by the fused low-layer kernel."""

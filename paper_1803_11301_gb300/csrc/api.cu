@@ -272,6 +272,7 @@ struct GraphEntry {
     u64 *c;
     void *ws;
     bool profiling;
+    unsigned gen;           // GraphCache::gen at capture
     cudaGraphExec_t exec;
     unsigned long long launches[STAGE_COUNT];
     std::vector<Rec> recs;
@@ -284,6 +285,7 @@ struct GraphCache {
     std::vector<Key> seen;              // keys called once, not captured yet
     cudaStream_t cap = nullptr;
     unsigned long long clock = 0;
+    unsigned gen = 0;                   // bumped by gf2x_tune_pin: older graphs hold other launch shapes
     bool disabled = false;
 };
 
@@ -549,7 +551,7 @@ gf2x_status op_graph(gf2x_ctx *ctx, int kind, const u64 *a, u64 na, const u64 *b
         return op_device(ctx, kind, a, na, b, nb, c, ws, st);
     for (GraphEntry &e : gc->entries) {
         if (e.kind == kind && e.a == a && e.b == b && e.na == na && e.nb == nb && e.c == c && e.ws == ws &&
-            e.profiling == ctx->profiling) {
+            e.profiling == ctx->profiling && e.gen == gc->gen) {
             e.stamp = ++gc->clock;
             if (cudaGraphLaunch(e.exec, st) != cudaSuccess) return GF2X_ECUDA;
             for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
@@ -614,6 +616,7 @@ gf2x_status op_graph(gf2x_ctx *ctx, int kind, const u64 *a, u64 na, const u64 *b
         gc->entries.erase(gc->entries.begin() + (long)old);
     }
     e.stamp = ++gc->clock;
+    e.gen = gc->gen;
     gc->entries.push_back(e);
     GraphEntry &ent = gc->entries.back();
     if (cudaGraphLaunch(ent.exec, st) != cudaSuccess) return GF2X_ECUDA;
@@ -717,6 +720,7 @@ u64 hash_table(const std::vector<JobDev> &t, const void *ws)
 struct BatchGraph {
     u64 key;
     bool profiling;
+    unsigned gen;           // GraphCache::gen at capture
     cudaGraphExec_t exec;
     unsigned long long launches[STAGE_COUNT];
     std::vector<Rec> recs;
@@ -911,6 +915,21 @@ gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen)
 {
     if (!ctx) return GF2X_EINVAL;
     gf2x::tuner_freeze(ctx->tuner, frozen != 0);
+    return GF2X_OK;
+}
+
+static_assert(GF2X_KNOB_UNIT16_R == gf2x::TUNE_UNIT16_R && GF2X_KNOB_BOTTOM_SHAPE == gf2x::TUNE_BOTTOM_SHAPE &&
+                  GF2X_KNOB_WINDOW_DEPTH == gf2x::TUNE_WINDOW_DEPTH &&
+                  GF2X_KNOB_M128_BOTTOM_CHUNK == gf2x::TUNE_M128_BOTTOM_CHUNK &&
+                  GF2X_KNOB_BOTTOM_DEPTH == gf2x::TUNE_BFLY_DEPTH &&
+                  GF2X_KNOB_M128_BOTTOM_DEPTH == gf2x::TUNE_M128_BFLY_DEPTH,
+              "the ABI's knob numbers are the tuner's");
+
+gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice)
+{
+    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_M128_BOTTOM_DEPTH || choice < -1) return GF2X_EINVAL;
+    gf2x::tuner_pin(ctx->tuner, knob, choice);
+    ++graphs(ctx)->gen;           // captured graphs keep their shapes: capture again
     return GF2X_OK;
 }
 
@@ -1243,7 +1262,7 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         return run_all(st);
     const u64 key = hash_table(bp.table, ws);
     for (BatchGraph &e : bc->entries)
-        if (e.key == key && e.profiling == ctx->profiling) {
+        if (e.key == key && e.profiling == ctx->profiling && e.gen == gc->gen) {
             e.stamp = ++gc->clock;
             TRY(cudaGraphLaunch(e.exec, st));
             for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
@@ -1297,6 +1316,7 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         bc->entries.erase(bc->entries.begin() + (long)old);
     }
     e.stamp = ++gc->clock;
+    e.gen = gc->gen;
     bc->entries.push_back(e);
     BatchGraph &ent = bc->entries.back();
     TRY(cudaGraphLaunch(ent.exec, st));

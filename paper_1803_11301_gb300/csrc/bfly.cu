@@ -520,8 +520,9 @@ void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int c
 {
     const u64 tiles = 1ull << (l - bt);
     int shape = tiles * (u64)count < 4 * (u64)ctx->num_sms ? 1 : 0;
-    if (scratch) {
-        static const int cands[3] = {1, 0, 2};
+    static const int cands[3] = {1, 0, 2};
+    if (!scratch) shape = tune_pinned(ctx, TUNE_BOTTOM_SHAPE, cands, 3, shape);
+    else {
         shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, (tune_bucket(tiles * (u64)count) << 2) | (u64)mode, cands, 3, shape,
                             [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, st); },
                             st);
@@ -607,13 +608,23 @@ static int depth_or_default(int bt, int l)   // bt < 0: the default depth
     return l < bt ? l : bt;
 }
 
+// A depth pinned by gf2x_tune_pin if it is one of the candidates for l (8 ..
+// min(kBottom, l)), else fallback.
+static int pinned_depth(gf2x_ctx *ctx, int l, int fallback)
+{
+    int cands[kBottom];
+    int nc = 0;
+    for (int b = kMinDepth; b <= kBottom && b <= l; ++b) cands[nc++] = b;
+    return tune_pinned(ctx, TUNE_BFLY_DEPTH, cands, nc, fallback);
+}
+
 // Forward (or inverse) Butterfly of `count` transforms of 2^l points each,
 // `stride` words apart.
 cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st,
                       u64 *scratch)
 {
     configure();
-    const int bt = default_depth(l);
+    const int bt = pinned_depth(ctx, l, default_depth(l));
     if (!inverse) {
         cudaError_t e = top_passes(ctx, x, nullptr, l, bt, false, count, stride, st);
         if (e != cudaSuccess) return e;
@@ -638,7 +649,8 @@ cudaError_t butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64
 int butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
 {
     if (l <= kMinDepth) return l;
-    return tune_stored(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth(l));
+    return pinned_depth(ctx, l,
+                        tune_stored(ctx, TUNE_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth(l)));
 }
 
 int butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count, u64 stride, cudaStream_t st)

@@ -475,8 +475,9 @@ cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int 
 {
     const u64 blocks = (L >> 16) * (u64)count;
     int R = blocks <= 4 * (u64)ctx->num_sms ? 8 : 32;
-    if (scratch) {
-        static const int cands[3] = {8, 16, 32};
+    static const int cands[3] = {8, 16, 32};
+    if (!scratch) R = tune_pinned(ctx, TUNE_UNIT16_R, cands, 3, R);
+    else {
         R = tune_choice(ctx, TUNE_UNIT16_R, (tune_bucket(blocks) << 1) | (inverse ? 1u : 0u), cands, 3, R,
                         [&](int r) { return basis_cvt_unit16_r(ctx, scratch, L, inverse, count, stride, r, st); }, st);
     }

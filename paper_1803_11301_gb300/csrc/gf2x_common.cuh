@@ -194,13 +194,18 @@ inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] +
 namespace gf2x {
 
 // Autotuner (tune.cu).  Knobs: the choices it measures.
+// The same numbers as the GF2X_KNOB_* constants of the C ABI.
 enum TuneKnob {
     TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3, TUNE_M128_BOTTOM_CHUNK = 4, TUNE_BFLY_DEPTH = 5,
-    TUNE_M128_BFLY_DEPTH = 6
+    TUNE_M128_BFLY_DEPTH = 6, TUNE_KNOB_END = 7
 };
 void *tuner_create();
 void tuner_destroy(void *t);
 void tuner_freeze(void *t, bool frozen);
+// choice < 0 releases the knob.
+void tuner_pin(void *t, int knob, int choice);
+// The pinned choice of `knob` if it is one of cands, else fallback.
+int tune_pinned(gf2x_ctx *ctx, int knob, const int *cands, int ncand, int fallback);
 // The stored choice for (knob, key); else, when measuring is possible, runs
 // run(candidate) on `st` for every candidate, stores and returns the fastest;
 // else `fallback`.

@@ -646,8 +646,9 @@ cudaError_t launch_bottom128(gf2x_ctx *ctx, u64 *X, const u64 *Y, int l, int bt,
 {
     const u64 tiles = (1ull << (l - bt)) * (u64)count;
     int chunk = tiles > 2 * (u64)ctx->num_sms ? kChunkSmall128 : kChunkLarge128;
-    if (scratch) {
-        static const int cands[2] = {kChunkLarge128, kChunkSmall128};
+    static const int cands[2] = {kChunkLarge128, kChunkSmall128};
+    if (!scratch) chunk = tune_pinned(ctx, TUNE_M128_BOTTOM_CHUNK, cands, 2, chunk);
+    else {
         chunk = tune_choice(ctx, TUNE_M128_BOTTOM_CHUNK, (tune_bucket(tiles) << 2) | (u64)mode, cands, 2, chunk,
                             [&](int ch) {
                                 return launch_bottom128_chunk(ctx, scratch, Y, l, bt, mode, count, stride, ch, st);
@@ -826,10 +827,21 @@ static int depth_or_default128(int bt, int l)   // bt < 0: the default depth
     return l < bt ? l : bt;
 }
 
+// A depth pinned by gf2x_tune_pin if it is one of the candidates for l (8 ..
+// min(kBottom128, l)), else fallback.
+static int pinned_depth128(gf2x_ctx *ctx, int l, int fallback)
+{
+    int cands[kBottom128];
+    int nc = 0;
+    for (int b = kMinDepth128; b <= kBottom128 && b <= l; ++b) cands[nc++] = b;
+    return tune_pinned(ctx, TUNE_M128_BFLY_DEPTH, cands, nc, fallback);
+}
+
 int m128_butterfly_depth_stored(gf2x_ctx *ctx, int l, int count)
 {
     if (l <= kMinDepth128) return l;
-    return tune_stored(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth128(l));
+    return pinned_depth128(
+        ctx, l, tune_stored(ctx, TUNE_M128_BFLY_DEPTH, ((u64)l << 32) | tune_bucket((u64)count), default_depth128(l)));
 }
 
 // The whole schedule (top passes of both forward transforms, fused bottom
@@ -856,7 +868,7 @@ int m128_butterfly_depth(gf2x_ctx *ctx, u64 *X, u64 *Y, u64 *T, int l, int count
 cudaError_t m128_butterfly(gf2x_ctx *ctx, u64 *x, int l, bool inverse, int count, u64 stride, cudaStream_t st)
 {
     configure128();
-    const int bt = default_depth128(l);
+    const int bt = pinned_depth128(ctx, l, default_depth128(l));
     if (!inverse) {
         cudaError_t e = top_passes128(ctx, x, nullptr, l, bt, false, count, stride, st);
         if (e != cudaSuccess) return e;

@@ -14,6 +14,8 @@
 // GF2X_TUNE=0 in the environment turns measuring off (the built-in defaults
 // are then used); gf2x_tune_freeze stops it for one context (a server tunes
 // during its warm-up, then freezes so that no request waits on a measurement).  The first call of a new shape synchronises its stream.
+// gf2x_tune_pin fixes one knob's choice wherever it is among that call's
+// candidates (reproducible launch shapes; tests run every variant this way).
 #include <cstdlib>
 #include <vector>
 
@@ -28,10 +30,13 @@ struct TuneEntry {
     int choice;
 };
 
+constexpr int kKnobs = TUNE_KNOB_END;
+
 struct TuneCache {
     std::vector<TuneEntry> entries;
     bool disabled = false;    // GF2X_TUNE=0: never measure
     bool frozen = false;      // gf2x_tune_freeze: stored choices and defaults only
+    int pinned[kKnobs] = {};  // gf2x_tune_pin: 0 = not pinned, else the choice + 1
 };
 
 TuneCache *cache(gf2x_ctx *ctx) { return (TuneCache *)ctx->tuner; }
@@ -57,6 +62,20 @@ void tuner_freeze(void *t, bool frozen)
     if (t) ((TuneCache *)t)->frozen = frozen;
 }
 
+void tuner_pin(void *t, int knob, int choice)
+{
+    if (t && knob > 0 && knob < kKnobs) ((TuneCache *)t)->pinned[knob] = choice < 0 ? 0 : choice + 1;
+}
+
+int tune_pinned(gf2x_ctx *ctx, int knob, const int *cands, int ncand, int fallback)
+{
+    TuneCache *c = cache(ctx);
+    if (!c || knob <= 0 || knob >= kKnobs || !c->pinned[knob]) return fallback;
+    for (int i = 0; i < ncand; ++i)
+        if (cands[i] == c->pinned[knob] - 1) return cands[i];
+    return fallback;
+}
+
 int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback)
 {
     TuneCache *c = cache(ctx);
@@ -71,6 +90,8 @@ int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, i
 {
     TuneCache *c = cache(ctx);
     if (!c) return fallback;
+    const int pin = tune_pinned(ctx, knob, cands, ncand, -1);
+    if (pin >= 0) return pin;
     for (const TuneEntry &e : c->entries)
         if (e.knob == knob && e.key == key) return e.choice;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -61,6 +61,19 @@ def test_null_context_rejected(lib):
     assert lib.gf2x_mul(None, None, 1, None, 1, None, None, 0, None) == 1      # EINVAL
     assert lib.gf2x_basis_cvt(None, None, 64, None) == 1
     assert lib.gf2x_ctx_create(None, 0) == 1
+    assert lib.gf2x_tune_pin(None, 5, 9) == 1
+    assert lib.gf2x_tune_freeze(None, 1) == 1
+
+
+def test_knob_constants_match_the_header():
+    import re
+    from paper_1803_11301_gb300 import (KNOB_BOTTOM_DEPTH, KNOB_BOTTOM_SHAPE, KNOB_M128_BOTTOM_CHUNK,
+                                        KNOB_M128_BOTTOM_DEPTH, KNOB_UNIT16_R, KNOB_WINDOW_DEPTH)
+    text = open(HEADER).read()
+    want = {k: int(v) for k, v in re.findall(r"GF2X_KNOB_(\w+) = (\d+)", text)}
+    assert want == {"UNIT16_R": KNOB_UNIT16_R, "BOTTOM_SHAPE": KNOB_BOTTOM_SHAPE, "WINDOW_DEPTH": KNOB_WINDOW_DEPTH,
+                    "M128_BOTTOM_CHUNK": KNOB_M128_BOTTOM_CHUNK, "BOTTOM_DEPTH": KNOB_BOTTOM_DEPTH,
+                    "M128_BOTTOM_DEPTH": KNOB_M128_BOTTOM_DEPTH}
 
 
 def test_no_device_path_reports_enodev(lib):
