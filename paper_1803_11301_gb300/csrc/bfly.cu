@@ -5,7 +5,7 @@
 // coordinates right by i) and alpha = v_{l+32}:
 //     c = v_{l+32-i} + (element with Cantor coordinates 2 blk).
 //
-// Top passes (layers >= kBottom): a pass covers m <= 4 consecutive layers
+// Top passes (layers >= bt, the bottom depth): a pass covers m <= 4 consecutive layers
 // [p, p+m).  The points it touches are split into columns: for fixed high
 // bits (>= p+m) and fixed low bits (< p), the 2^m points that differ in bits
 // [p, p+m) form one column, held by one thread in registers through all m
@@ -13,12 +13,15 @@
 // twiddles of the pass, so the block builds one multiplication table per
 // twiddle and reuses it for every column of the group.
 //
-// Bottom tile (layers < kBottom): 2^kBottom consecutive points in shared
-// memory, one layer after the other.  Layers i >= kTableMin (twiddle shared by
-// 2^i butterflies per array) use tables, built 32 at a time; layers
-// 0..kTableMin-1 multiply with the integer form.  In the fused mode the tile holds the matching tiles of both
-// transforms: forward A, forward B, pointwise product, inverse (the Butterfly,
-// pointwise and iButterfly steps of Alg. 5 on the low layers) in one pass over HBM.
+// Bottom tile (layers < bt; bt = l up to l = 8, else 8 <= bt <= kBottom): 2^bt points in
+// shared memory.  Layers i >= kTableMin (twiddle shared by 2^i butterflies per
+// array) use tables, packed so that the top layers' tables are built in one
+// round and the inverse starts with the tables the forward pass left; layers
+// 0..kTableMin-1 multiply with the integer form, in registers (one
+// shared-memory pass each for tiles under 64 points).  In the fused
+// mode the tile holds the matching tiles of both transforms: forward A,
+// forward B, pointwise product, inverse (the Butterfly, pointwise and
+// iButterfly steps of Alg. 5 on the low layers) in one pass over HBM.
 //
 // Multiplication table (method of four Russians, Sec. 4.5): for a fixed c,
 // tab[w][e] = c * (e x^(4w)) for the 16 four-bit windows w and e < 16, so
@@ -213,45 +216,6 @@ __device__ __forceinline__ void tile_layer(u64 *a, int bt, int i, u64 ctop, cons
     }
 }
 
-// Layer i >= kTableMin on the tile(s): the 2^(bt-1-i) twiddles of the layer
-// c_j = v_{l+32-i} + Cantor((base >> i) + 2j) get tables CHUNK at a time;
-// each chunk's butterflies run on every array of the pass (A and B together).
-template <int CHUNK>
-__device__ void table_layer(u64 *a, u64 *b, int bt, int i, int l, u64 base, const u64 *__restrict__ cvt,
-                            const u64 *__restrict__ vb, u64 *tabs, bool inverse)
-{
-    const int ntot = 1 << (bt - 1 - i);
-    const int span = 1 << i;
-    const u64 vtop = vb[l + 32 - i];
-    for (int j0 = 0; j0 < ntot; j0 += CHUNK) {
-        const int nt = ntot - j0 < CHUNK ? ntot - j0 : CHUNK;
-        build_tables(tabs, nt, [&](int t) { return vtop ^ cantor(cvt, (base >> i) + ((u64)(j0 + t) << 1)); });
-        for (int t = threadIdx.x; t < (nt << i); t += blockDim.x) {
-            const int blk = j0 + (t >> i), jj = t & (span - 1);
-            const int s0 = (blk << (i + 1)) + jj;
-            const unsigned tb = smem_addr(tabs) + (unsigned)((blk - j0) * kTab * 8);
-            u64 x0 = a[s0], x1 = a[s0 + span];
-            if (!inverse) {
-                x0 ^= mul_tab(tb, x1);
-                x1 ^= x0;
-            } else {
-                x1 ^= x0;
-                x0 ^= mul_tab(tb, x1);
-            }
-            a[s0] = x0;
-            a[s0 + span] = x1;
-            if (b) {
-                u64 y0 = b[s0], y1 = b[s0 + span];
-                y0 ^= mul_tab(tb, y1);
-                y1 ^= y0;
-                b[s0] = y0;
-                b[s0 + span] = y1;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // Butterflies of layer i for the blocks j0 .. j0 + nt - 1 of the tile(s),
 // block j's table at slot slot0 + j - j0 of tabs; on A and, if given, B.
 __device__ __forceinline__ void table_butterflies(u64 *a, u64 *b, int i, int j0, int nt, int slot0, const u64 *tabs,
@@ -297,6 +261,7 @@ __device__ void table_layers(u64 *a, u64 *b, int bt, const u64 *__restrict__ cvt
 {
     static_assert(CHUNK == 8 || CHUNK == 16 || CHUNK == 32, "chunk of 8, 16 or 32 tables");
     constexpr int kLogChunk = CHUNK == 8 ? 3 : CHUNK == 16 ? 4 : 5;
+    if (bt <= kTableMin) return;
     const int lo_top = bt - kLogChunk > kTableMin ? bt - kLogChunk : kTableMin;
     auto twid = [&](int i, int j) {
         const unsigned j2 = (unsigned)j << 1;
@@ -444,16 +409,15 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom
         for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
         return;
     }
+    // tiles below 64 points (transforms of at most 2^11 bits): the layers one
+    // shared-memory pass each
+    const int low = bt < kTableMin ? bt : kTableMin;   // layers below `low` multiply in integer form
     if (mode != BOTTOM_INV) {
-        for (int i = bt - 1; i >= 0; --i) {
-            if (i >= kTableMin) {
-                table_layer<CHUNK>(a, fwd_b ? b : nullptr, bt, i, l, base, cvt, vb, tabs, false);
-            } else {
-                const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
-                tile_layer(a, bt, i, ctop, cvt, false);
-                if (fwd_b) tile_layer(b, bt, i, ctop, cvt, false);
-                __syncthreads();
-            }
+        table_layers<CHUNK>(a, fwd_b ? b : nullptr, bt, cvt, ctops, tabs, false, false);
+        for (int i = low - 1; i >= 0; --i) {
+            tile_layer(a, bt, i, ctops[i], cvt, false);
+            if (fwd_b) tile_layer(b, bt, i, ctops[i], cvt, false);
+            __syncthreads();
         }
     }
     if (fused) {
@@ -461,15 +425,11 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) k_bfly_bottom
         __syncthreads();
     }
     if (mode != BOTTOM_FWD) {
-        for (int i = 0; i < bt; ++i) {
-            if (i >= kTableMin) {
-                table_layer<CHUNK>(a, nullptr, bt, i, l, base, cvt, vb, tabs, true);
-            } else {
-                const u64 ctop = vb[l + 32 - i] ^ cantor(cvt, base >> i);
-                tile_layer(a, bt, i, ctop, cvt, true);
-                __syncthreads();
-            }
+        for (int i = 0; i < low; ++i) {
+            tile_layer(a, bt, i, ctops[i], cvt, true);
+            __syncthreads();
         }
+        table_layers<CHUNK>(a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);
     }
     for (int k = threadIdx.x; k < T; k += blockDim.x) X[base + k] = a[k];
 }
