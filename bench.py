@@ -60,7 +60,7 @@ METRIC = "operand Gbit/s (na+nb bits per product / time)"
 UNIT = "Gbit/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# Measured peaks (MEASURED_PEAKS.json is written on the GPU machine; these are its values).
+# Peaks measured on GB300 (the copy bandwidth and SM clock of MEASURED_PEAKS.json; used when it is absent).
 HBM_PEAK_GBS_FALLBACK = 6784.5
 SM_MAX_MHZ_FALLBACK = 2070.0
 NUM_SMS = 152
