@@ -95,3 +95,45 @@ def test_m128_size_rules_match_the_oracle(lib):
     assert m128_transform_bits(0, 5) == 0 and m128_workspace_bytes(7, 0) == 0
     assert m128_workspace_bytes(1 << 37, (1 << 37) + 2) == 0       # n = 2^39 > 2^38
     assert lib.gf2x_mul_m128(None, None, 1, None, 1, None, None, 0, None) == 1      # EINVAL
+
+
+def _jobs(specs):
+    """gf2x_job array from (a, na, b, nb, c) with integer addresses (never dereferenced here)."""
+    from paper_1803_11301_gb300 import Job
+    arr = (Job * len(specs))()
+    for k, (a, na, b, nb, c) in enumerate(specs):
+        arr[k] = Job(a, na, b, nb, c)
+    return arr
+
+
+def test_batch_workspace_rules(lib):
+    # host-side planning of gf2x_mul_batch: a pure function of the job lengths,
+    # room for every job's three transform buffers (a single product's
+    # workspace less its 256 reserved bytes), 0 for an invalid job
+    from paper_1803_11301_gb300 import workspace_bytes
+    A, B, C = 1 << 32, 2 << 32, 3 << 32                       # disjoint, 8-byte aligned addresses
+    lens = [(1000, 5000), (1 << 20, 1 << 20), (64, 64), (1 << 20, 77), (3, 70000)]
+    specs = [(A + 2**24 * k, na, B + 2**24 * k, nb, C + 2**24 * k) for k, (na, nb) in enumerate(lens)]
+    ws = lib.gf2x_batch_workspace_bytes(_jobs(specs), len(specs))
+    assert ws >= sum(workspace_bytes(na, nb) - 256 for na, nb in lens) + 256
+    moved = [(a + 4096, na, b + 8192, nb, c + 65536) for a, na, b, nb, c in specs]
+    assert lib.gf2x_batch_workspace_bytes(_jobs(moved), len(moved)) == ws        # lengths only
+    shuffled = [specs[k] for k in (3, 0, 4, 2, 1)]
+    assert lib.gf2x_batch_workspace_bytes(_jobs(shuffled), len(shuffled)) == ws  # order-free
+    with_empty = specs + [(A, 0, B, 100, C), (A, 100, B, 0, C)]
+    assert lib.gf2x_batch_workspace_bytes(_jobs(with_empty), len(with_empty)) == ws
+    one = lib.gf2x_batch_workspace_bytes(_jobs(specs[:1]), 1)
+    assert workspace_bytes(1000, 5000) <= one < ws
+    assert lib.gf2x_batch_workspace_bytes(_jobs([(A + 4, 1000, B, 5000, C)]), 1) == 0          # misaligned a
+    assert lib.gf2x_batch_workspace_bytes(_jobs([(A, 1000, B, 5000, A + 8)]), 1) == 0          # c overlaps a
+    assert lib.gf2x_batch_workspace_bytes(_jobs([(A, 1 << 36, B, (1 << 36) + 2, C)]), 1) == 0  # n > 2^37
+    assert lib.gf2x_batch_workspace_bytes(None, 0) == lib.gf2x_batch_workspace_bytes(_jobs([]), 0)
+
+
+def test_host_workspace_holds_the_staging_buffers(lib):
+    # gf2x_mul_host stages pageable operands and the product in its workspace
+    from paper_1803_11301_gb300 import host_workspace_bytes, workspace_bytes
+    for na, nb in [(1, 1), (1000, 5000), (1 << 20, 77), (1 << 24, 1 << 24)]:
+        words = (na + 63) // 64 + (nb + 63) // 64 + (na + nb - 1 + 63) // 64
+        assert host_workspace_bytes(na, nb) >= workspace_bytes(na, nb) + 8 * words
+    assert host_workspace_bytes(0, 9) == 0
