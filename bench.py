@@ -1,8 +1,9 @@
 """Benchmark: GF(2)[x] products on GB300 through the C ABI.
 
-Default workload: one product of two seeded uniform-random 2^24-bit
-polynomials per step (the 2^24 x 2^24 configuration); ``--config 1`` / ``3``
-select 2^16 x 2^16 and 2^30 x 2^30.  Prints ONE JSON line (rank 0).
+Default workload: one product of two seeded uniform-random 2^30-bit
+polynomials per step (the 2^30 x 2^30 configuration, the largest single
+product of the workload list); ``--config 1`` / ``2`` select 2^16 x 2^16 and
+2^24 x 2^24.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gf2x|reference]
 
@@ -77,16 +78,44 @@ PRODUCTS_PER_SM_CLOCK_128 = 0.25
 BOTTOM_LAYERS_128 = 10
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a stage's
-# kernel, keyed by (stage, na, nb, field bits, bottom layers), from one capture of the same workload
-# (profiles/k_bfly_bottom_gf2x_mul_2e30x2e30.md, profiles/k128_bfly_bottom_gf2x_mul_m128_2e30x2e30.md,
-# profiles/launch_list_gf2x_mul_2e24x2e24.md, profiles/launch_list_gf2x_mul_m128_2e24x2e24.md).
-# An entry is removed when its kernel changes; a missing entry reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers)
-    ("bottom_fused", 1 << 24, 1 << 24, 64, 9): 8468224 + 0,
-    ("bottom_fused", 1 << 24, 1 << 24, 128, 9): 8488192 + 0,
-    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): 538430976 + 225118720,
-    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): 537023232 + 225316096,
+# kernel, keyed by (stage, na, nb, field bits, bottom layers), from one ncu
+# capture of the same workload (the summaries under profiles/ give the
+# commands).  Each entry carries the digest of the kernel's sources at capture
+# time (comments and blank space stripped, see source_digest): when the
+# sources have changed since, the line reports traffic null and says so.
+KERNEL_SOURCES = {64: ["paper_1803_11301_gb300/csrc/bfly.cu", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"],
+                  128: ["paper_1803_11301_gb300/csrc/m128.cu", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"]}
+TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers): (bytes, source digest)
+    ("bottom_fused", 1 << 24, 1 << 24, 64, 9): (8468224 + 0, "0"),
+    ("bottom_fused", 1 << 24, 1 << 24, 128, 9): (8488192 + 0, "0"),
+    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): (538430976 + 225118720, "0"),
+    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): (537023232 + 225316096, "0"),
 }
+
+
+def source_digest(field: int) -> str:
+    """Digest of the dominant kernel's sources, comments and blank space removed."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[field]:
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
+    return h.hexdigest()[:16]
+
+
+def traffic_entry(key, field: int):
+    """(bytes per launch or None, note) for the roofline's traffic field."""
+    ent = TRAFFIC_BYTES_PER_LAUNCH.get(key)
+    if ent is None:
+        return None, "no ncu capture of this kernel at this workload"
+    nbytes, digest = ent
+    if digest != source_digest(field):
+        return None, "stale: the kernel's sources changed since the ncu capture"
+    return nbytes, "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this workload"
 
 
 def load_peaks():
@@ -341,6 +370,18 @@ def stage_work(stage, na, nb, n, products, field=64, bottom_layers=None):
     return 0, "hbm"
 
 
+def whole_product_alu(n, field, ms_per_step, mul_peak):
+    """The whole product against the product-rate roofline: Alg. 5 needs
+    1.5 l n_p + n_p field products (three transforms of l layers, n_p/2
+    butterflies each, and the pointwise step)."""
+    l = n.bit_length() - 1 - (7 if field == 128 else 6)
+    n_p = 1 << l
+    products = 3 * l * (n_p // 2) + n_p
+    achieved = products / (ms_per_step / 1e3) / 1e9
+    return {"products": products, "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s",
+            "frac": achieved / mul_peak}
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_1803_11301_gb300 import Context, build as lib_build
@@ -463,19 +504,21 @@ def run_gpu(args, world, rank, local):
                         "work_per_step": work / args.steps}
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
+    traffic, traffic_note = traffic_entry((dom, na, nb, field, bottom_layers), field)
+    per_clock = PRODUCTS_PER_SM_CLOCK_128 if field == 128 else PRODUCTS_PER_SM_CLOCK
+    mul_peak = NUM_SMS * per_clock * sm_max_mhz * 1e6 / 1e9
     if d["bound"] == "mul":
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
-        per_clock = PRODUCTS_PER_SM_CLOCK_128 if field == 128 else PRODUCTS_PER_SM_CLOCK
-        peak = NUM_SMS * per_clock * sm_max_mhz * 1e6 / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmul/s", "frac": achieved / peak,
+        roof = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s", "frac": achieved / mul_peak,
                 "peak_source": (f"derived: {NUM_SMS} SMs x {sm_max_mhz:.0f} MHz x {per_clock:g} GF(2^{field}) "
-                                "product per SM-clock (shared-memory port bound of the table product)"),
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field, bottom_layers)), "kernel_stage": dom,
+                                "product per SM-clock (shared-memory port bound of the table product, "
+                                "bench.py --stage field_mul)"),
+                "traffic": traffic, "traffic_note": traffic_note, "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
     else:
         achieved = d["work_per_step"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": f"{peak_src} copy bandwidth", "traffic": TRAFFIC_BYTES_PER_LAUNCH.get((dom, na, nb, field, bottom_layers)),
+                "peak_source": f"{peak_src} copy bandwidth", "traffic": traffic, "traffic_note": traffic_note,
                 "kernel_stage": dom,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches_per_step"], 1)}
 
@@ -489,7 +532,9 @@ def run_gpu(args, world, rank, local):
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"{world} independent replica(s)"},
             "hbm_compulsory": {"bytes_per_product": compulsory,
-                               "frac": compulsory / (ms_per_step / 1e3) / 1e9 / hbm_peak},
+                               "frac": compulsory / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+                               "peak_gbs": hbm_peak, "peak_source": f"{peak_src} copy bandwidth"},
+            "alu_whole_product": whole_product_alu(n, field, ms_per_step, mul_peak),
             "roofline": roof, "stages_ms": {k: round(v["ms"], 4) for k, v in stages.items()},
             "profiled_ms_per_step": prof_total_ms / args.steps,
             "gpu_launches": int(launches), "clocks": clk, "e2e": e2e}
@@ -500,6 +545,40 @@ def run_gpu(args, world, rank, local):
                                 "sample": f"{done} whole {ona}x{onb}-bit products, portable C Karatsuba, OpenMP"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_field_mul(args):
+    """The GF(2^64) product forms (gf2x_bench_field_mul), each timed on the same
+    chains of products by a fixed element; the measurement behind the
+    product-rate peak of the roofline (the four-bit-window table form)."""
+    import torch
+    from paper_1803_11301_gb300 import Context, build as lib_build
+    lib_build.build()
+    ctx = Context(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    rows = []
+    for v in range(len(Context.FIELD_VARIANTS)):
+        steps = args.field_steps if Context.FIELD_VARIANTS[v] != "bitslice" else max(1, args.field_steps // 8)
+        best = None
+        for _ in range(3):
+            r = ctx.bench_field_mul(v, steps)
+            if best is None or r["ms"] < best["ms"]:
+                best = r
+        rows.append(best)
+    clk = clocks.stop()
+    mhz = clk.get("sm_mhz") or SM_MAX_MHZ_FALLBACK
+    ref = rows[0]["checksum"]
+    for r in rows:
+        r["gmul_s"] = r["products"] / (r["ms"] / 1e3) / 1e9
+        r["mul_per_sm_clock"] = r["gmul_s"] * 1e9 / (NUM_SMS * mhz * 1e6)
+        r["checksum_matches_int"] = r["checksum"] == ref
+    torch.cuda.synchronize()
+    print(json.dumps({"stage": "field_mul", "what": "dependent chains x <- c x, 4 per thread, 8 blocks of 256 "
+                      "threads per SM; products / CUDA-event time of one launch (best of 3)",
+                      "variants": rows, "clocks": clk}), flush=True)
     ctx.close()
 
 
@@ -853,19 +932,25 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf2x", choices=["gf2x", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
+    ap.add_argument("--config", type=int, default=3, choices=sorted(CONFIGS))
     ap.add_argument("--batch", type=int, default=4096, help="products per batch for --config 4")
     ap.add_argument("--requests", type=int, default=2000, help="requests for --config 5")
     ap.add_argument("--load", type=float, default=0.8, help="arrival rate / saturated rate for --config 5")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage", default=None,
-                    choices=["butterfly", "ibutterfly", "basis_cvt", "ibasis_cvt", "encode", "decode", "pointwise"],
-                    help="time one stage alone through its entry point (profiling aid)")
+                    choices=["butterfly", "ibutterfly", "basis_cvt", "ibasis_cvt", "encode", "decode", "pointwise",
+                             "field_mul"],
+                    help="time one stage alone through its entry point (profiling aid); field_mul: every "
+                         "GF(2^64) product form")
+    ap.add_argument("--field-steps", type=int, default=2000, help="chain steps per thread for --stage field_mul")
     ap.add_argument("--log2-points", type=int, default=24, help="n_p = 2^this GF(2^64) points for --stage")
     ap.add_argument("--log2-bits", type=int, default=None,
                     help="operands of 2^this bits for the single-product configs (1-3, 7, 8): the length sweep")
     args = ap.parse_args()
+    if args.stage == "field_mul":
+        run_field_mul(args)
+        return
     if args.stage:
         run_stage(args)
         return

@@ -105,10 +105,12 @@ GF2X_API gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits
                      void *workspace, size_t ws_bytes, void *stream);
 
 /* The same product with HOST operands and result, synchronous.  Page-locked
- * (pinned or registered) buffers are read and written by the product's load
- * and store kernels directly over the CPU-GPU link; pageable buffers are
- * copied into the device workspace and the result copied back.  Either way
- * the call returns once c holds the product.  The workspace must hold
+ * (pinned or registered) buffers that are 8-byte aligned, with c apart from a
+ * and b, are read and written by the product's load and store kernels
+ * directly over the CPU-GPU link; other buffers (pageable, unaligned or
+ * overlapping) are copied into the device workspace and the result copied
+ * back.  Host pointers need no particular alignment.  Either way the call
+ * returns once c holds the product.  The workspace must hold
  * gf2x_host_workspace_bytes(na, nb) bytes. */
 GF2X_API size_t gf2x_host_workspace_bytes(uint64_t na_bits, uint64_t nb_bits);
 GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na_bits,
@@ -119,10 +121,12 @@ GF2X_API gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64
  * no counterpart: this is a deployment convenience.  Some callers cannot call
  * cudaMalloc or any allocator: a framework that has reserved the whole device
  * for its own memory pool, or a code path where entering an allocator is not
- * allowed.  This call takes no workspace: it runs gf2x_mul on a fixed scratch
- * array of 3 * GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8 + 256 bytes (768 KiB) that lives in
- * the library's device memory; every GPU that loads the library holds that
- * array until the process exits.  It allocates nothing.
+ * allowed.  This call takes no workspace: it runs gf2x_mul's kernels on a fixed
+ * scratch array of 3 * GF2X_NOALLOC_MAX_TRANSFORM_BITS / 8 + 256 bytes (768 KiB)
+ * that lives in the library's device memory; every GPU that loads the library
+ * holds that array until the process exits.  It allocates nothing: the kernels
+ * are launched one by one on every call, never from a captured CUDA graph
+ * (instantiating one may allocate device memory).
  *   Limit: transform length n <= GF2X_NOALLOC_MAX_TRANSFORM_BITS (2^21 bits,
  *   e.g. two operands of 2^20 bits); larger products return GF2X_ETOOBIG and
  *   enqueue nothing.  Other arguments and results as for gf2x_mul.
@@ -147,12 +151,17 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
  * n_bits (n_bits / 8, one uint64 per point), 0 unless n_bits is a power of
  * two with 64 <= n_bits <= 2^37.
  *
+ * gf2x_transform_workspace_bytes(n_bits): the device workspace that
+ *   gf2x_forward_transform needs at transform length n_bits (3 buffers of
+ *   n_bits/8 bytes and 256 bytes of device state; the same as a product with
+ *   that transform length), 0 when gf2x_transform_bytes is 0.
+ *
  * gf2x_forward_transform: bhat (device, gf2x_transform_bytes(n_bits) bytes,
  *   8-byte aligned, disjoint from b and the workspace) <- the transform of b
  *   (nb_bits bits, 1 <= nb_bits <= n_bits) at length n_bits.  Use n_bits =
  *   gf2x_transform_bits(na, nb_bits) for products with na-bit operands; the
- *   workspace of such a product (gf2x_workspace_bytes(na, nb_bits), or
- *   3 n_bits/8 + 256 bytes, 256-aligned) suffices.  Asynchronous.
+ *   workspace must hold gf2x_transform_workspace_bytes(n_bits) bytes,
+ *   256-aligned (the workspace of such a product suffices).  Asynchronous.
  *
  * gf2x_mul_transformed: c = a * b, with b given as bhat = its transform at
  *   gf2x_transform_bits(na_bits, nb_bits) (the caller keeps bhat consistent
@@ -163,6 +172,7 @@ GF2X_API gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64_t
  *   entry point for this; it is Alg. 5 with b's forward steps done
  *   ahead of time. */
 GF2X_API size_t gf2x_transform_bytes(uint64_t n_bits);
+GF2X_API size_t gf2x_transform_workspace_bytes(uint64_t n_bits);
 GF2X_API gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb_bits, uint64_t n_bits,
                                             uint64_t *bhat, void *workspace, size_t ws_bytes, void *stream);
 GF2X_API gf2x_status gf2x_mul_transformed(gf2x_ctx *ctx, const uint64_t *a, uint64_t na_bits, const uint64_t *bhat,
@@ -247,6 +257,28 @@ GF2X_API gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice);
  * the default before that.  -1 for a NULL context or an empty or too long
  * product.  Informational (profiling and roofline accounting). */
 GF2X_API int gf2x_bottom_layers(gf2x_ctx *ctx, uint64_t na_bits, uint64_t nb_bits);
+
+/* Field-multiply measurement (a benchmark, not part of the product path): the
+ * GF(2^64) product forms this GPU offers, timed on the same work.  The paper
+ * multiplies with PCLMULQDQ (Sec. 4.3) and, by a fixed element, with 4-bit
+ * table lookups (Sec. 4.5); GB300 has no carry-less multiply instruction.
+ * Every variant runs 4 dependent chains x <- c x per thread (one fixed c) for
+ * `steps` steps (1 .. 2^20) over 8 blocks of 256 threads per SM, one launch
+ * on `stream` timed with CUDA events after an untimed launch; all variants
+ * give the same *checksum (an XOR of the final values).  *ms = the launch's
+ * time, *products = the field products it computed.  Synchronous.
+ *   variant 0  32x32 integer multiplies on operands with 3-bit holes, Karatsuba
+ *           1  the same with the fixed operand's masks computed once
+ *           2  16 four-bit windows of a per-element table in shared memory
+ *              (the form the Butterfly kernels use for shared twiddles)
+ *           3  8 eight-bit windows (2 KiB per window)
+ *           4  low half by four-bit windows, high half by integer multiplies
+ *           5  16x16 integer multiplies on operands with 2-bit holes
+ *           6  64 elements of a warp bit-sliced across its lanes; the product
+ *              by c as its 64x64 GF(2) matrix, planes fetched by warp shuffles
+ * GF2X_EINVAL for a NULL pointer, an unknown variant or steps out of range. */
+GF2X_API gf2x_status gf2x_bench_field_mul(gf2x_ctx *ctx, int variant, int steps, uint64_t *checksum,
+                                          double *ms, uint64_t *products, void *stream);
 
 /* ------------------------------------------------------------------------
  * Per-stage profiling.  Stage k (0 <= k < gf2x_stage_count()) is one step of

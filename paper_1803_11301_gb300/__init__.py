@@ -43,6 +43,7 @@ ABI_FUNCTIONS = {
     "gf2x_mul_host": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_mul_noalloc": (_ST, [_P, _P, _U64, _P, _U64, _P, _P]),
     "gf2x_transform_bytes": (_SZ, [_U64]),
+    "gf2x_transform_workspace_bytes": (_SZ, [_U64]),
     "gf2x_forward_transform": (_ST, [_P, _P, _U64, _U64, _P, _P, _SZ, _P]),
     "gf2x_mul_transformed": (_ST, [_P, _P, _U64, _P, _U64, _P, _P, _SZ, _P]),
     "gf2x_batch_workspace_bytes": (_SZ, [_P, _SZ]),
@@ -68,6 +69,8 @@ ABI_FUNCTIONS = {
     "gf2x_m128_butterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_m128_ibutterfly": (_ST, [_P, _P, _U64, _P]),
     "gf2x_m128_pointwise": (_ST, [_P, _P, _P, _P, _U64, _P]),
+    "gf2x_bench_field_mul": (_ST, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_U64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64), _P]),
     "gf2x_stage_count": (ctypes.c_int, []),
     "gf2x_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
     "gf2x_profile_enable": (_ST, [_P, ctypes.c_int]),
@@ -267,7 +270,9 @@ class Context:
         """The transform of b (the BasisCvt, Encode and Butterfly steps of Alg. 5) at transform length n, for reuse."""
         if out is None:
             out = self.empty_words(n // 64)
-        need = 3 * ((n // 8 + 255) // 256 * 256) + 256
+        need = int(self._lib.gf2x_transform_workspace_bytes(n))
+        if need == 0:
+            raise Gf2xError(1, "gf2x_transform_workspace_bytes")
         if workspace is None:
             workspace = self.workspace(need)
         _check(self._lib.gf2x_forward_transform(self._h, self._tensor_ptr(b, _words(nb), "b"), nb, n,
@@ -325,6 +330,16 @@ class Context:
         la = (_U64 * n)()
         self._lib.gf2x_profile_read(self._h, ms, la, n)
         return {self._lib.gf2x_stage_name(k).decode(): (ms[k], int(la[k])) for k in range(n)}
+
+    FIELD_VARIANTS = ("int", "int_const", "tab4", "tab8", "hybrid", "int16", "bitslice")
+
+    def bench_field_mul(self, variant: int, steps: int, stream=None) -> dict:
+        """Time one GF(2^64) product form (gf2x_bench_field_mul): checksum, ms, products."""
+        cs, ms, pr = _U64(), ctypes.c_double(), _U64()
+        _check(self._lib.gf2x_bench_field_mul(self._h, int(variant), int(steps), ctypes.byref(cs), ctypes.byref(ms),
+                                              ctypes.byref(pr), self._stream(stream)), "gf2x_bench_field_mul")
+        return {"variant": self.FIELD_VARIANTS[variant], "checksum": int(cs.value), "ms": ms.value,
+                "products": int(pr.value)}
 
     def selftest_wait_timeout(self, stream=None):
         """Launch a bounded wait that must run out; the status word then reads GF2X_ETIMEOUT."""

@@ -717,8 +717,21 @@ u64 hash_table(const std::vector<JobDev> &t, const void *ws)
     return h ^ (u64)t.size();
 }
 
+// A batch graph is replayed only for the same job table and workspace: the
+// hash picks candidates, the stored table decides.
+struct BatchKey {
+    u64 hash;
+    const void *ws;
+    std::vector<JobDev> table;
+    bool same(u64 h, const void *w, const std::vector<JobDev> &t) const
+    {
+        return hash == h && ws == w && table.size() == t.size() &&
+               (t.empty() || std::memcmp(table.data(), t.data(), t.size() * sizeof(JobDev)) == 0);
+    }
+};
+
 struct BatchGraph {
-    u64 key;
+    BatchKey key;
     bool profiling;
     unsigned gen;           // GraphCache::gen at capture
     cudaGraphExec_t exec;
@@ -729,7 +742,7 @@ struct BatchGraph {
 
 struct BatchCache {
     std::vector<BatchGraph> entries;
-    std::vector<u64> seen;
+    std::vector<BatchKey> seen;
 };
 
 constexpr size_t kMaxBatchGraphs = 8;
@@ -820,6 +833,7 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
         return fail(GF2X_ENOMEM);
     }
     ctx->d_sync = (GridSync *)((char *)ctx->d_status + 128);
+    ctx->d_word = (unsigned long long *)((char *)ctx->d_status + 192);
     ctx->d_cvt = ctx->d_tables;
     ctx->d_enc = ctx->d_tables + 2048;
     ctx->d_dec = ctx->d_tables + 4096;
@@ -890,12 +904,18 @@ size_t gf2x_workspace_bytes(uint64_t na, uint64_t nb)
     return 3 * buffer_bytes(n) + kAlign;          // + 256 bytes reserved for device-side state
 }
 
-gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *c,
-                     void *ws, size_t ws_bytes, void *stream)
+// Argument rules of gf2x_mul; GF2X_OK when the product may be enqueued
+// (*empty set when there is nothing to compute).
+static gf2x_status check_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb,
+                             const uint64_t *c, const void *ws, size_t ws_bytes, bool *empty)
 {
+    *empty = false;
     if (!ctx) return GF2X_EINVAL;
     const u64 nc = product_bits(na, nb);
-    if (!nc) return GF2X_OK;
+    if (!nc) {
+        *empty = true;
+        return GF2X_OK;
+    }
     const u64 n = transform_bits(na, nb);
     if (n > kMaxTransformBits) return GF2X_ETOOBIG;
     if (!a || !b || !c || !ws || !aligned8(a) || !aligned8(b) || !aligned8(c) || ((uintptr_t)ws % kAlign))
@@ -906,6 +926,15 @@ gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64
     if (overlap(c, cb, a, (size_t)((na + 63) / 64) * 8) || overlap(c, cb, b, (size_t)((nb + 63) / 64) * 8) ||
         overlap(c, cb, ws, need))
         return GF2X_EINVAL;
+    return GF2X_OK;
+}
+
+gf2x_status gf2x_mul(gf2x_ctx *ctx, const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *c,
+                     void *ws, size_t ws_bytes, void *stream)
+{
+    bool empty = false;
+    const gf2x_status s = check_mul(ctx, a, na, b, nb, c, ws, ws_bytes, &empty);
+    if (s != GF2X_OK || empty) return s;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GF2X_ECUDA;
     return op_graph(ctx, OP_MUL, a, na, b, nb, c, ws, (cudaStream_t)stream);
@@ -946,6 +975,11 @@ size_t gf2x_transform_bytes(uint64_t n)
     return valid_n(n) ? (size_t)(n / 8) : 0;
 }
 
+size_t gf2x_transform_workspace_bytes(uint64_t n)
+{
+    return valid_n(n) ? 3 * buffer_bytes(n) + kAlign : 0;
+}
+
 gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb, uint64_t n, uint64_t *bhat,
                                    void *ws, size_t ws_bytes, void *stream)
 {
@@ -953,7 +987,7 @@ gf2x_status gf2x_forward_transform(gf2x_ctx *ctx, const uint64_t *b, uint64_t nb
     if (n > kMaxTransformBits) return GF2X_ETOOBIG;
     if (!valid_n(n) || nb == 0 || nb > n) return GF2X_EINVAL;
     if (!b || !bhat || !ws || !aligned8(b) || !aligned8(bhat) || ((uintptr_t)ws % kAlign)) return GF2X_EINVAL;
-    const size_t need = 3 * buffer_bytes(n) + kAlign;
+    const size_t need = gf2x_transform_workspace_bytes(n);
     if (ws_bytes < need) return GF2X_ENOSPACE;
     const size_t tb = (size_t)(n / 8);
     if (overlap(bhat, tb, b, (size_t)((nb + 63) / 64) * 8) || overlap(bhat, tb, ws, need)) return GF2X_EINVAL;
@@ -1018,7 +1052,14 @@ gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, co
     };
     const u64 *va = (const u64 *)device_view(a_host), *vb = (const u64 *)device_view(b_host);
     u64 *vc = (u64 *)device_view(c_host);
-    if (va && vb && vc) {
+    // The kernels read and write whole words, so the direct path needs the same
+    // pointer rules as gf2x_mul (8-byte alignment, c apart from a and b); other
+    // page-locked buffers take the staged path like pageable ones.
+    const size_t cbytes = (size_t)((nc + 63) / 64) * 8;
+    const bool direct = va && vb && vc && aligned8(va) && aligned8(vb) && aligned8(vc) &&
+                        !overlap(vc, cbytes, va, (size_t)((na + 63) / 64) * 8) &&
+                        !overlap(vc, cbytes, vb, (size_t)((nb + 63) / 64) * 8);
+    if (direct) {
         gf2x_status s = op_graph(ctx, OP_MUL, va, na, vb, nb, vc, ws, st);
         if (s != GF2X_OK) return s;
         TRY(cudaStreamSynchronize(st));
@@ -1262,7 +1303,7 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         return run_all(st);
     const u64 key = hash_table(bp.table, ws);
     for (BatchGraph &e : bc->entries)
-        if (e.key == key && e.profiling == ctx->profiling && e.gen == gc->gen) {
+        if (e.key.same(key, ws, bp.table) && e.profiling == ctx->profiling && e.gen == gc->gen) {
             e.stamp = ++gc->clock;
             TRY(cudaGraphLaunch(e.exec, st));
             for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
@@ -1272,19 +1313,19 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         }
     bool repeat = false;
     for (size_t k = 0; k < bc->seen.size(); ++k)
-        if (bc->seen[k] == key) {
+        if (bc->seen[k].same(key, ws, bp.table)) {
             repeat = true;
             bc->seen.erase(bc->seen.begin() + (long)k);
             break;
         }
     if (!repeat) {
         if (bc->seen.size() >= 32) bc->seen.erase(bc->seen.begin());
-        bc->seen.push_back(key);
+        bc->seen.push_back(BatchKey{key, ws, bp.table});
         return run_all(st);
     }
     if (!gc->cap && cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking) != cudaSuccess) return run_all(st);
     BatchGraph e{};
-    e.key = key;
+    e.key = BatchKey{key, ws, bp.table};
     e.profiling = ctx->profiling;
     unsigned long long before[STAGE_COUNT];
     for (int k = 0; k < STAGE_COUNT; ++k) before[k] = ctx->launches[k];
@@ -1325,6 +1366,27 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         for (const Rec &r : ent.recs) p->pending.push_back(r);
     return GF2X_OK;
 }
+
+}  // extern "C"
+
+namespace gf2x {
+
+// gf2x_mul without its CUDA graph cache: the kernels are launched one by one
+// on every call (instantiating a graph may allocate device memory).
+gf2x_status mul_uncached(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                         size_t ws_bytes, cudaStream_t st)
+{
+    bool empty = false;
+    const gf2x_status s = check_mul(ctx, a, na, b, nb, c, ws, ws_bytes, &empty);
+    if (s != GF2X_OK || empty) return s;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GF2X_ECUDA;
+    return op_device(ctx, OP_MUL, a, na, b, nb, c, ws, st);
+}
+
+}  // namespace gf2x
+
+extern "C" {
 
 const char *gf2x_stage_name(int stage)
 {

@@ -22,10 +22,12 @@ typedef uint32_t u32;
 #define GF2X_MOD_LOW 0x1Bull   // x^4 + x^3 + x + 1
 
 // ------------------------------------------------------------ field arithmetic
-// 32 x 32 -> 64-bit carry-less product.  a_i = a & (0x1111... << i) keeps one
-// bit in four; the integer product a_i * b_j has at most 8 terms per output
-// position, so each count fits in the 4-bit gap and its parity is the
-// carry-less bit.  Positions of class k (mod 4) come from the pairs i+j = k.
+// 32 x 32 -> 64-bit carry-less product by integer multiplication of operands
+// with "holes", the published constant-time technique of T. Pornin (BearSSL's
+// ghash_ctmul): a_i = a & (0x1111... << i) keeps one bit in four; the integer
+// product a_i * b_j has at most 8 terms per output position, so each count
+// fits in the 4-bit gap and its parity is the carry-less bit.  Positions of
+// class k (mod 4) come from the pairs i+j = k.
 __device__ __forceinline__ u64 clmul32(u32 a, u32 b)
 {
     const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
@@ -167,6 +169,7 @@ struct gf2x_ctx {
     u64 *d_cantor;      // v_0 .. v_63
     int *d_status;      // device status word (gf2x_status)
     GridSync *d_sync;   // barrier state for the stage entry points
+    unsigned long long *d_word;   // one device word for measurement checksums (fieldbench.cu)
     u64 cantor[64];     // host copy of the Cantor basis
     // GF(2^128) variant (m128.cu): 128-bit entries as (lo, hi) word pairs
     u64 *d_tables128;   // one allocation holding the tables below
@@ -294,5 +297,10 @@ cudaError_t m128_butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, const u64 *Y, int
 cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st,
                                        int bt = -1);
 cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
+
+// gf2x_mul (same arguments and checks) with every kernel launched directly,
+// never through the CUDA graph cache (api.cu).
+gf2x_status mul_uncached(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
+                         size_t ws_bytes, cudaStream_t st);
 
 }  // namespace gf2x

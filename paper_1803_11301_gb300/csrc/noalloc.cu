@@ -7,6 +7,9 @@
 // from the caller: its scratch is a fixed array in device memory, defined
 // below, that every GPU loading this library holds until the process exits.
 //
+// The product runs the kernels of gf2x_mul one by one on every call: it never
+// captures or instantiates a CUDA graph, since instantiation may allocate.
+//
 // The array's name is only a host-side stand-in in host code, not a device
 // address, so host code never passes it to a kernel.  The first call on each
 // device, with that device current, asks the runtime for the array's device
@@ -58,5 +61,7 @@ extern "C" gf2x_status gf2x_mul_noalloc(gf2x_ctx *ctx, const uint64_t *a, uint64
     gf2x_status s = scratch_address(ctx->device, &scratch);
     if (prev != ctx->device) cudaSetDevice(prev);
     if (s != GF2X_OK) return s;
-    return gf2x_mul(ctx, a, na_bits, b, nb_bits, c, scratch, kScratchBytes, stream);
+    // Direct launches: gf2x_mul would capture and instantiate a CUDA graph from
+    // the second identical call on, and instantiation may allocate.
+    return gf2x::mul_uncached(ctx, a, na_bits, b, nb_bits, c, scratch, kScratchBytes, (cudaStream_t)stream);
 }

@@ -137,3 +137,13 @@ def test_host_workspace_holds_the_staging_buffers(lib):
         words = (na + 63) // 64 + (nb + 63) // 64 + (na + nb - 1 + 63) // 64
         assert host_workspace_bytes(na, nb) >= workspace_bytes(na, nb) + 8 * words
     assert host_workspace_bytes(0, 9) == 0
+
+
+def test_transform_workspace_rule(lib):
+    # gf2x_forward_transform's workspace: what a product of that transform length needs
+    from paper_1803_11301_gb300 import workspace_bytes
+    for n in [64, 128, 1 << 17, 1 << 25, 1 << 37]:
+        assert lib.gf2x_transform_workspace_bytes(n) == workspace_bytes(n // 2, n // 2)
+        assert lib.gf2x_transform_bytes(n) == n // 8
+    for bad in [0, 32, 96, 1000, 1 << 38]:
+        assert lib.gf2x_transform_workspace_bytes(bad) == 0

@@ -30,3 +30,26 @@ def test_byte_stages_and_whole_job_value():
     work, kind = bench.stage_work("encode", 1 << 24, 1 << 24, n, 1)
     assert kind == "hbm" and work == 2 * 2 * n // 8                  # two operands: read n bits, write n_p words
     assert bench.whole_job_value(1000, 2.0, 4, scale=1.0) == 2000.0   # 4 ranks x 1000 units / 2 s
+
+
+def test_whole_product_alu_counts_alg5_products():
+    for field, na in [(64, 1 << 24), (64, 1 << 30), (128, 1 << 30)]:
+        n = 2 * na
+        l = n.bit_length() - 1 - (7 if field == 128 else 6)
+        r = bench.whole_product_alu(n, field, 1.0, 100.0)
+        assert r["products"] == 1.5 * l * (1 << l) + (1 << l)
+        assert abs(r["frac"] - r["achieved"] / 100.0) < 1e-12
+
+
+def test_traffic_entry_goes_null_when_the_kernel_changes():
+    key = ("bottom_fused", 1 << 30, 1 << 30, 64, 11)
+    saved = bench.TRAFFIC_BYTES_PER_LAUNCH[key]
+    try:
+        bench.TRAFFIC_BYTES_PER_LAUNCH[key] = (123, bench.source_digest(64))
+        assert bench.traffic_entry(key, 64)[0] == 123
+        bench.TRAFFIC_BYTES_PER_LAUNCH[key] = (123, "0" * 16)
+        nbytes, note = bench.traffic_entry(key, 64)
+        assert nbytes is None and note.startswith("stale")
+    finally:
+        bench.TRAFFIC_BYTES_PER_LAUNCH[key] = saved
+    assert bench.traffic_entry(("bottom_fused", 5, 5, 64, 1), 64)[0] is None

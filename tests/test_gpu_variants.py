@@ -171,3 +171,10 @@ def test_basis_cvt_knobs(ctx, pins):
         for rep in range(2):
             got = host(ctx.mul(da, n, db, n))
             assert np.array_equal(got, want), (r, w, rep)
+
+
+def test_field_multiply_forms_agree(ctx):
+    # every GF(2^64) product form of the measurement computes the same chains
+    sums = [ctx.bench_field_mul(v, 3)["checksum"] for v in range(len(ctx.FIELD_VARIANTS))]
+    assert len(set(sums)) == 1, sums
+    assert ctx.stream_status() == 0

@@ -4,8 +4,8 @@ Some callers cannot call cudaMalloc or any allocator (a framework that owns the
 whole device through its own pool, or a path where entering an allocator is not
 allowed).  gf2x_mul_noalloc runs the same product on a fixed scratch array inside
 the library.  This test calls it through the C ABI twice in a row, on different
-operands, and checks each result bit for bit against gf2x_mul (exact integer work,
-so the tolerance is zero).  It also checks that a product above the stated limit
+operands, and checks each result bit for bit against gf2x_mul and against the CPU
+oracle (exact integer work, so the tolerance is zero).  It also checks that a product above the stated limit
 is refused with GF2X_ETOOBIG.  The file name makes pytest collect it last.
 """
 import ctypes
@@ -42,19 +42,23 @@ def _ptr(t):
 
 def test_noalloc_matches_gf2x_mul_twice(env):
     import torch
+    from oracle import clmul as O
     lib, ctx = env
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     cases = [(1 << 20, (1 << 20) - 5, 11), (777, 4093, 12)]       # two calls in a row
     for na, nb, k in cases:
-        a = _dev(synth.operand(synth.config_seed(77, 2 * k), na))
-        b = _dev(synth.operand(synth.config_seed(77, 2 * k + 1), nb))
+        ah = synth.operand(synth.config_seed(77, 2 * k), na)
+        bh = synth.operand(synth.config_seed(77, 2 * k + 1), nb)
+        a, b = _dev(ah), _dev(bh)
         nc = na + nb - 1
         want = ctx.mul(a, na, b, nb)
         got = torch.zeros((nc + 63) // 64, dtype=torch.int64, device="cuda")
         status = lib.gf2x_mul_noalloc(ctx._h, _ptr(a), na, _ptr(b), nb, _ptr(got), stream)
         assert status == 0, status
         torch.cuda.synchronize()
-        assert torch.equal(got, want), (na, nb)
+        assert torch.equal(got, want), (na, nb)                    # the existing entry point's result
+        got_h = got.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got_h, O.mul(ah, na, bh, nb)), (na, nb)   # and the CPU oracle's
 
 
 def test_noalloc_rejects_products_above_the_limit(env):
