@@ -565,16 +565,19 @@ def run_field_mul(args):
         best = None
         for _ in range(3):
             r = ctx.bench_field_mul(v, steps)
+            r["steps"] = steps
             if best is None or r["ms"] < best["ms"]:
                 best = r
         rows.append(best)
     clk = clocks.stop()
     mhz = clk.get("sm_mhz") or SM_MAX_MHZ_FALLBACK
-    ref = rows[0]["checksum"]
+    ref = {}                                     # variant 0's checksum per chain length
     for r in rows:
+        if r["steps"] not in ref:
+            ref[r["steps"]] = ctx.bench_field_mul(0, r["steps"])["checksum"]
         r["gmul_s"] = r["products"] / (r["ms"] / 1e3) / 1e9
         r["mul_per_sm_clock"] = r["gmul_s"] * 1e9 / (NUM_SMS * mhz * 1e6)
-        r["checksum_matches_int"] = r["checksum"] == ref
+        r["checksum_matches_variant0"] = r["checksum"] == ref[r["steps"]]
     torch.cuda.synchronize()
     print(json.dumps({"stage": "field_mul", "what": "dependent chains x <- c x, 4 per thread, 8 blocks of 256 "
                       "threads per SM; products / CUDA-event time of one launch (best of 3)",
@@ -642,32 +645,42 @@ def run_batch(args, world, rank, local):
     ws = torch.empty(ctx.batch_workspace_bytes(jobs), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     prepared = ctx.prepare_batch(jobs)       # argument marshalling once, outside the timed region
-    ctx.profile_enable(True)
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        ctx.mul_batch(prepared, workspace=ws, stream=stream)
-    torch.cuda.synchronize(dev)
-    ctx.profile_enable(True)
+    from paper_1803_11301_gb300 import KNOB_BATCH_PERSISTENT
+
+    def timed_batch(mode):
+        """K batch calls, one persistent launch each (mode 1) or one launch per kernel and size class (0)."""
+        ctx.tune_pin(KNOB_BATCH_PERSISTENT, mode)
+        ctx.profile_enable(True)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            ctx.mul_batch(prepared, workspace=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        ctx.profile_enable(True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        dist_barrier(world)
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k)
+            starts[k].record(stream)
+            ctx.mul_batch(prepared, workspace=ws, stream=stream)
+            ends[k].record(stream)
+            ctx.profile_read()
+        torch.cuda.synchronize(dev)
+        dist_barrier(world)
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        ctx.tune_pin(KNOB_BATCH_PERSISTENT, -1)
+        return dist_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world), prof
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    dist_barrier(world)
-    torch.cuda.synchronize(dev)
-    for k in range(args.steps):
-        flush.fill_(k)
-        starts[k].record(stream)
-        ctx.mul_batch(prepared, workspace=ws, stream=stream)
-        ends[k].record(stream)
-        ctx.profile_read()
-    torch.cuda.synchronize(dev)
-    dist_barrier(world)
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
+    class_ms, class_prof = timed_batch(0)
+    total_ms, prof = timed_batch(1)
     clk = clocks.stop()
-    total_ms = dist_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world)
     value = world * count * args.steps / (total_ms / 1e3)
+    class_value = world * count * args.steps / (class_ms / 1e3)
     # one gf2x_mul per product (sequential calls on the same stream), one pass after one warm-up pass
     wsp = torch.empty(max(workspace_bytes(j[1], j[3]) for j in jobs), dtype=torch.uint8, device=dev)
     for j in jobs:
@@ -733,11 +746,15 @@ def run_batch(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": CONFIGS[4]["name"], "products": count,
                        "l2": "flushed before every timed step (256 MiB write)"},
+            "batch_mode": "one persistent launch per batch (device work queue)",
+            "class_launches": {"value": class_value, "unit": "products/s", "ms_per_step": class_ms / args.steps,
+                               "gpu_launches": int(sum(v[1] for v in class_prof.values()) / args.steps),
+                               "how": "the same call with one launch per kernel and size class, graph replay"},
             "plain": {"value": plain, "unit": "products/s", "how": "one gf2x_mul call per product, same stream"},
             "batched_over_plain": value / plain,
             "operand_gbits": world * sum(j[1] + j[3] for j in jobs) * args.steps / (total_ms / 1e3) / 1e9,
             "stages_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
-            "gpu_launches": int(launches), "clocks": clk,
+            "gpu_launches": int(launches / args.steps), "clocks": clk,
             "e2e": {"value": world * count * args.steps / e2e_s, "unit": "products/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h}}
     if rank == 0:
@@ -823,7 +840,9 @@ def run_reuse(args, world, rank, local):
 
 
 def run_serving(args, world, rank, local):
-    """Continuous batching vs one gf2x_mul per request, same Poisson arrival stream."""
+    """Continuous batching under Poisson arrivals at several loads, against one
+    gf2x_mul per request on the same arrival stream, and end to end with host
+    operands (copies in and out inside each request's latency)."""
     import torch
     from paper_1803_11301_gb300 import Context, build as lib_build, workspace_bytes
     from paper_1803_11301_gb300.serving import Server, Request, percentile
@@ -833,22 +852,40 @@ def run_serving(args, world, rank, local):
     ctx = Context(local)
     count = args.requests
     sizes = serving_requests(count, 7 + rank)
-    # device-resident operand pools; a request uses a prefix of a pool entry
-    small = [torch.from_numpy(synth.operand(synth.config_seed(5, 100 + k), 1 << 26).view(np.int64)).to(dev)
-             for k in range(8)]
-    big = [torch.from_numpy(synth.operand(synth.config_seed(5, 200 + k), 1 << 28).view(np.int64)).to(dev)
-           for k in range(2)]
+    # operand pools (device, and page-locked host copies for the e2e leg); a
+    # request uses a prefix of a pool entry
+    small_h = [synth.operand(synth.config_seed(5, 100 + k), 1 << 26) for k in range(8)]
+    big_h = [synth.operand(synth.config_seed(5, 200 + k), 1 << 28) for k in range(2)]
+    small = [torch.from_numpy(w.view(np.int64)).to(dev) for w in small_h]
+    big = [torch.from_numpy(w.view(np.int64)).to(dev) for w in big_h]
+    small_p = [torch.from_numpy(w.view(np.int64)).pin_memory() for w in small_h]
+    big_p = [torch.from_numpy(w.view(np.int64)).pin_memory() for w in big_h]
 
-    def operand(bits, k):
-        pool = big if bits > (1 << 26) else small
-        return pool[k % len(pool)]
+    def pool_of(bits, host):
+        if bits > (1 << 26):
+            return (big_p if host else big), 1000
+        return (small_p if host else small), 0
 
-    def make(k):
+    def operand(bits, k, host=False):
+        pool, base = pool_of(bits, host)
+        t = pool[k % len(pool)]
+        return t[: (bits + 63) // 64], base + k % len(pool)
+
+    rng_reuse = synth.uniform01(synth.config_seed(5, 77), count)
+
+    def make(k, host=False):
         na, nb = sizes[k]
-        return Request(operand(na, 3 * k), na, operand(nb, 3 * k + 1), nb, tag=k)
+        a, _ = operand(na, 3 * k, host)
+        if args.reuse_frac > 0 and rng_reuse[k] < args.reuse_frac:
+            b, key = operand(nb, 0, host)             # one recurring b per pool and length
+        else:
+            b, key = operand(nb, 3 * k + 1, host)
+        return Request(a, na, b, nb, tag=k, host=host, b_key=(key, nb) if args.reuse_frac > 0 else None)
 
-    # saturated: everything queued at once
-    srv = Server(ctx, streams=3)
+    def server():
+        return Server(ctx, streams=3, reuse_after=2 if args.reuse_frac > 0 else 0)
+
+    srv = server()
     for k in range(min(count, 400)):                        # warm-up
         srv.submit(make(k))
     srv.drain()
@@ -857,19 +894,19 @@ def run_serving(args, world, rank, local):
         ctx.mul(r.a, r.na, r.b, r.nb)
     torch.cuda.synchronize(dev)
     ctx.tune_freeze(True)       # launch shapes measured in the warm-up; no request waits on a measurement
-    srv = Server(ctx, streams=3)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # saturated: everything queued at once
+    srv = server()
     t0 = time.perf_counter()
     for k in range(count):
         srv.submit(make(k))
     srv.drain()
-    sat_s = time.perf_counter() - t0
-    sat = count / sat_s
-    # arrivals: Poisson at 0.8 x saturated
-    lam = args.load * sat
-    gaps = -np.log(1.0 - synth.uniform01(synth.config_seed(5, 55), count)) / lam
-    arrivals = np.cumsum(gaps)
+    sat = count / (time.perf_counter() - t0)
+    gaps01 = -np.log(1.0 - synth.uniform01(synth.config_seed(5, 55), count))
 
-    def replay(submit_fn, poll_fn, done_fn):
+    def replay(arrivals, submit_fn, poll_fn, done_fn):
         start = time.perf_counter()
         k = 0
         while k < count or not done_fn():
@@ -880,19 +917,25 @@ def run_serving(args, world, rank, local):
             poll_fn()
         return time.perf_counter() - start
 
-    srv = Server(ctx, streams=3)
-    reqs = []
+    def served_at(load, host=False):
+        arrivals = np.cumsum(gaps01 / (load * sat))
+        s2 = server()
+        reqs = []
 
-    def s_submit(k, t):
-        r = make(k)
-        r.arrival = t
-        reqs.append(r)
-        srv.submit(r)
-    wall = replay(s_submit, srv.poll, lambda: not srv.pending and not srv.inflight)
-    lat = [1e3 * (r.done - r.arrival) for r in reqs]
-    served = {"products_per_s": count / wall, "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-              "batches": srv._next_batch}
-    # one gf2x_mul per request, in arrival order on one stream
+        def s_submit(k, t):
+            r = make(k, host)
+            r.arrival = t
+            reqs.append(r)
+            s2.submit(r)
+        wall = replay(arrivals, s_submit, s2.poll, lambda: not s2.pending and not s2.inflight)
+        lat = [1e3 * (r.done - r.arrival) for r in reqs if r.state == "done"]
+        return {"load": load, "arrival_rate_per_s": load * sat, "products_per_s": count / wall,
+                "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "batches": s2._next_batch,
+                "rejected": len(s2.rejected), "reused": sum(1 for r in reqs if r.reused)}
+
+    loads = {str(x): served_at(x) for x in (0.5, 0.8, 1.0)}
+    headline = loads["0.8"]
+    # one gf2x_mul per request, in arrival order on one stream, at 0.8 x saturated
     stream = torch.cuda.current_stream(dev)
     wsp = torch.empty(max(workspace_bytes(na, nb) for na, nb in sizes), dtype=torch.uint8, device=dev)
     plain_pending = []
@@ -901,7 +944,8 @@ def run_serving(args, world, rank, local):
     def p_submit(k, t):
         na, nb = sizes[k]
         out = torch.empty((na + nb - 1 + 63) // 64, dtype=torch.int64, device=dev)
-        ctx.mul(operand(na, 3 * k), na, operand(nb, 3 * k + 1), nb, out=out, workspace=wsp, stream=stream)
+        r = make(k)
+        ctx.mul(r.a, na, r.b, nb, out=out, workspace=wsp, stream=stream)
         ev = torch.cuda.Event()
         ev.record(stream)
         plain_pending.append((t, ev, out))
@@ -911,16 +955,25 @@ def run_serving(args, world, rank, local):
         while plain_pending and plain_pending[0][1].query():
             t, _, _ = plain_pending.pop(0)
             plain_lat.append(1e3 * (now - t))
-    pwall = replay(p_submit, p_poll, lambda: not plain_pending)
+    pwall = replay(np.cumsum(gaps01 / (0.8 * sat)), p_submit, p_poll, lambda: not plain_pending)
     plain = {"products_per_s": count / pwall, "p50_ms": percentile(plain_lat, 50), "p99_ms": percentile(plain_lat, 99)}
-    line = {"metric": "products/s under Poisson load (continuous batching)", "value": served["products_per_s"],
+    # end to end: page-locked host operands, copies to and from the device inside the latency
+    e2e_run = served_at(0.8, host=True)
+    clk = clocks.stop()
+    h2d = sum(8 * ((na + 63) // 64 + (nb + 63) // 64) for na, nb in sizes) / count
+    d2h = sum(8 * ((na + nb - 1 + 63) // 64) for na, nb in sizes) / count
+    line = {"metric": "products/s under Poisson load (continuous batching)", "value": headline["products_per_s"],
             "unit": "products/s", "n_gpus": world, "steps": count, "warmup": min(count, 400),
-            "ms_per_step": 1e3 * wall / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u64", "data": "synthetic",
-            "config": {"workload": CONFIGS[5]["name"], "requests": count, "load": args.load,
-                       "arrival_rate_per_s": lam, "saturated_products_per_s": sat},
-            "served": served, "plain_one_call_per_request": plain,
-            "e2e": None}
+            "ms_per_step": 1e3 / headline["products_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": CONFIGS[5]["name"], "requests": count, "load": 0.8,
+                       "saturated_products_per_s": sat, "reuse_frac": args.reuse_frac},
+            "served": headline, "loads": loads, "plain_one_call_per_request": plain,
+            "e2e": {"value": e2e_run["products_per_s"], "unit": "products/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "p50_ms": e2e_run["p50_ms"], "p99_ms": e2e_run["p99_ms"],
+                    "how": "page-locked host operands; the server copies them in and the product out on the "
+                           "batch's stream, inside each request's latency; bytes per request"},
+            "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -934,8 +987,9 @@ def main():
     ap.add_argument("--impl", default="gf2x", choices=["gf2x", "reference"])
     ap.add_argument("--config", type=int, default=3, choices=sorted(CONFIGS))
     ap.add_argument("--batch", type=int, default=4096, help="products per batch for --config 4")
-    ap.add_argument("--requests", type=int, default=2000, help="requests for --config 5")
-    ap.add_argument("--load", type=float, default=0.8, help="arrival rate / saturated rate for --config 5")
+    ap.add_argument("--requests", type=int, default=20000, help="requests for --config 5")
+    ap.add_argument("--reuse-frac", type=float, default=0.0,
+                    help="--config 5: share of requests whose b recurs (resident transforms); 0 keeps the workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage", default=None,

@@ -193,15 +193,25 @@ typedef struct gf2x_job {
 GF2X_API size_t gf2x_batch_workspace_bytes(const gf2x_job *jobs, size_t count);
 
 /* Many independent products of uneven lengths in one call (Alg. 5 for each).
- * The jobs are grouped by transform length n; every group runs the whole
- * path with one launch per kernel for all its jobs (the kernels' second grid
- * dimension is the job).  The host array `jobs` is read during the call and
- * copied to the workspace; every device buffer follows the gf2x_mul rules
- * (8-byte aligned, c disjoint from a, b and the workspace; jobs may share
- * operands but not results).  Jobs with na or nb = 0 write nothing.
- * Asynchronous.  From the second call with the same jobs (pointers and
- * lengths) and workspace on, the kernels replay from a captured CUDA graph
- * (at most 8 kept per context). */
+ * The jobs are grouped by transform length n (size classes).  By default the
+ * whole batch is ONE persistent kernel launch: the host plans every class's
+ * stages (load, BasisCvt, Encode, Butterfly with the pointwise product,
+ * Decode, iBasisCvt, store) as a device work queue, which a grid of one or
+ * two blocks per SM drains; a job's next stage starts as soon as that job's
+ * previous stage is done, and classes run side by side.  Every wait in the
+ * queue is bounded: if one runs out (it cannot in a correct plan) the launch
+ * records GF2X_ETIMEOUT in the context status word (gf2x_stream_status) and
+ * returns without finishing the batch.  Batches whose stages need a launch
+ * shape the persistent kernel lacks (transforms above 2^25 bits), or with
+ * GF2X_KNOB_BATCH_PERSISTENT pinned to 0, run one launch per kernel and class
+ * instead (the kernels' second grid dimension is the job).  Either way the
+ * results are the same.  The host array `jobs` is read during the call and
+ * copied to the workspace, with the queue; every device buffer follows the
+ * gf2x_mul rules (8-byte aligned, c disjoint from a, b and the workspace;
+ * jobs may share operands but not results).  Jobs with na or nb = 0 write
+ * nothing.  Asynchronous.  From the second call with the same jobs (pointers
+ * and lengths), workspace and plan on, the launches replay from a captured
+ * CUDA graph (at most 8 kept per context). */
 GF2X_API gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count,
                                     void *workspace, size_t ws_bytes, void *stream);
 
@@ -211,6 +221,13 @@ GF2X_API gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t 
  * word and returns, so the context stays usable; read it with
  * gf2x_stream_status.  The paper has no counterpart (failure detection). */
 GF2X_API gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream);
+
+/* Self-test of the persistent batch queue's bounded waits: launches a
+ * two-item queue whose second item waits on a first that can never finish.
+ * The wait gives up after 20 ms, records GF2X_ETIMEOUT in the context status
+ * word and the kernel returns; the context stays usable.  The paper has no
+ * counterpart (failure detection). */
+GF2X_API gf2x_status gf2x_selftest_queue_timeout(gf2x_ctx *ctx, void *stream);
 
 /* Read, and reset to GF2X_OK, the context's device status word after the
  * work already enqueued on `stream` has finished (synchronises the stream).
@@ -239,6 +256,8 @@ GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
  *   GF2X_KNOB_M128_BOTTOM_CHUNK  GF(2^128) bottom kernel tables per chunk: 4, 8
  *   GF2X_KNOB_BOTTOM_DEPTH       Butterfly layers in the bottom kernel: 8 .. 11
  *   GF2X_KNOB_M128_BOTTOM_DEPTH  the same for GF(2^128) points: 8 .. 10
+ *   GF2X_KNOB_BATCH_PERSISTENT   gf2x_mul_batch: 1 (one persistent launch, the
+ *                                default) or 0 (one launch per kernel and size class)
  * GF2X_EINVAL for a NULL context, an unknown knob or choice < -1.  Not
  * thread-safe against calls running on the same context. */
 enum {
@@ -247,7 +266,8 @@ enum {
     GF2X_KNOB_WINDOW_DEPTH = 3,
     GF2X_KNOB_M128_BOTTOM_CHUNK = 4,
     GF2X_KNOB_BOTTOM_DEPTH = 5,
-    GF2X_KNOB_M128_BOTTOM_DEPTH = 6
+    GF2X_KNOB_M128_BOTTOM_DEPTH = 6,
+    GF2X_KNOB_BATCH_PERSISTENT = 7
 };
 GF2X_API gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice);
 
@@ -268,12 +288,14 @@ GF2X_API int gf2x_bottom_layers(gf2x_ctx *ctx, uint64_t na_bits, uint64_t nb_bit
  * give the same *checksum (an XOR of the final values).  *ms = the launch's
  * time, *products = the field products it computed.  Synchronous.
  *   variant 0  32x32 integer multiplies on operands with 3-bit holes, Karatsuba
+ *              (the library's earlier integer form)
  *           1  the same with the fixed operand's masks computed once
  *           2  16 four-bit windows of a per-element table in shared memory
  *              (the form the Butterfly kernels use for shared twiddles)
  *           3  8 eight-bit windows (2 KiB per window)
  *           4  low half by four-bit windows, high half by integer multiplies
- *           5  16x16 integer multiplies on operands with 2-bit holes
+ *           5  16x16 integer multiplies on operands with 2-bit holes, Karatsuba
+ *              twice (the integer form the library uses)
  *           6  64 elements of a warp bit-sliced across its lanes; the product
  *              by c as its 64x64 GF(2) matrix, planes fetched by warp shuffles
  * GF2X_EINVAL for a NULL pointer, an unknown variant or steps out of range. */
@@ -283,7 +305,9 @@ GF2X_API gf2x_status gf2x_bench_field_mul(gf2x_ctx *ctx, int variant, int steps,
 /* ------------------------------------------------------------------------
  * Per-stage profiling.  Stage k (0 <= k < gf2x_stage_count()) is one step of
  * Alg. 5 as named by gf2x_stage_name(k): load, basis_cvt, encode, butterfly,
- * pointwise, ibutterfly, decode, ibasis_cvt, store.
+ * pointwise, ibutterfly, decode, ibasis_cvt, store, bottom_fused (the fused
+ * low Butterfly layers and pointwise product), persistent_batch (the whole
+ * persistent batch launch).
  * ---------------------------------------------------------------------- */
 GF2X_API int gf2x_stage_count(void);
 GF2X_API const char *gf2x_stage_name(int stage);

@@ -21,7 +21,7 @@ from .build import LIB as LIB_PATH
 __all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_bits", "workspace_bytes",
            "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
            "ABI_FUNCTIONS", "STATUS", "KNOB_UNIT16_R", "KNOB_BOTTOM_SHAPE", "KNOB_WINDOW_DEPTH",
-           "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH"]
+           "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH", "KNOB_BATCH_PERSISTENT"]
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
           5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE"}
@@ -50,6 +50,7 @@ ABI_FUNCTIONS = {
     "gf2x_mul_batch": (_ST, [_P, _P, _SZ, _P, _SZ, _P]),
     "gf2x_stream_status": (_ST, [_P, _P]),
     "gf2x_selftest_wait_timeout": (_ST, [_P, _P]),
+    "gf2x_selftest_queue_timeout": (_ST, [_P, _P]),
     "gf2x_basis_cvt": (_ST, [_P, _P, _U64, _P]),
     "gf2x_ibasis_cvt": (_ST, [_P, _P, _U64, _P]),
     "gf2x_encode": (_ST, [_P, _P, _U64, _P, _P]),
@@ -88,6 +89,7 @@ KNOB_WINDOW_DEPTH = 3          # 6, 7, 8
 KNOB_M128_BOTTOM_CHUNK = 4     # 4, 8
 KNOB_BOTTOM_DEPTH = 5          # 8 .. 11
 KNOB_M128_BOTTOM_DEPTH = 6     # 8 .. 10
+KNOB_BATCH_PERSISTENT = 7      # 1 (one persistent launch per batch), 0 (launches per kernel and size class)
 
 
 class Job(ctypes.Structure):
@@ -340,6 +342,10 @@ class Context:
                                               ctypes.byref(pr), self._stream(stream)), "gf2x_bench_field_mul")
         return {"variant": self.FIELD_VARIANTS[variant], "checksum": int(cs.value), "ms": ms.value,
                 "products": int(pr.value)}
+
+    def selftest_queue_timeout(self, stream=None):
+        """Launch a persistent-batch queue whose wait must run out; the status word then reads GF2X_ETIMEOUT."""
+        _check(self._lib.gf2x_selftest_queue_timeout(self._h, self._stream(stream)), "gf2x_selftest_queue_timeout")
 
     def selftest_wait_timeout(self, stream=None):
         """Launch a bounded wait that must run out; the status word then reads GF2X_ETIMEOUT."""

@@ -23,6 +23,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden", "--expt-relaxed-constexpr",
               "-I", INCLUDE]
+# The persistent batch kernel reads data that other blocks of the same launch
+# wrote: its global loads are cached in L2 only.
+PER_FILE_FLAGS = {"persist.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def nvcc() -> str:
@@ -56,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     for src in sources():
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *flags, *PER_FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -223,7 +223,7 @@ void record(Profiler *p, cudaEvent_t e, cudaStream_t st)
 void stage_begin(gf2x_ctx *ctx, int stage, cudaStream_t st)
 {
     ctx->stage = stage;
-    if (!ctx->profiling) return;
+    if (!ctx->profiling || ctx->rec) return;
     Profiler *p = profiler(ctx);
     cudaEvent_t e = take_event(p);
     if (!e) return;
@@ -234,7 +234,7 @@ void stage_begin(gf2x_ctx *ctx, int stage, cudaStream_t st)
 
 void stage_end(gf2x_ctx *ctx, cudaStream_t st)
 {
-    if (!ctx->profiling) return;
+    if (!ctx->profiling || ctx->rec) return;
     Profiler *p = profiler(ctx);
     if (!p->is_open) return;
     p->is_open = false;
@@ -633,6 +633,8 @@ struct BatchPlan {
     std::vector<JobDev> table;          // jobs in class order (ascending n)
     std::vector<ClassRun> runs;
     size_t table_bytes = 0;
+    size_t persist_off = 0;             // the persistent launch's area (segments, plans, counters)
+    size_t persist_bytes = 0;
     size_t total_bytes = 0;
 };
 
@@ -691,7 +693,9 @@ gf2x_status plan_batch(const gf2x_job *jobs, size_t count, BatchPlan &bp)
         bp.runs.push_back(r);
         k = e;
     }
-    bp.total_bytes = off;
+    bp.persist_off = off;
+    bp.persist_bytes = round_up(gf2x::persist_area_bytes(bp.runs.size(), bp.table.size()));
+    bp.total_bytes = off + bp.persist_bytes;
     return GF2X_OK;
 }
 
@@ -723,9 +727,10 @@ struct BatchKey {
     u64 hash;
     const void *ws;
     std::vector<JobDev> table;
-    bool same(u64 h, const void *w, const std::vector<JobDev> &t) const
+    u64 plan;                           // digest of the persistent launch's plan (0: class launches)
+    bool same(u64 h, const void *w, const std::vector<JobDev> &t, u64 p) const
     {
-        return hash == h && ws == w && table.size() == t.size() &&
+        return hash == h && ws == w && plan == p && table.size() == t.size() &&
                (t.empty() || std::memcmp(table.data(), t.data(), t.size() * sizeof(JobDev)) == 0);
     }
 };
@@ -828,12 +833,13 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     std::memcpy(&host[6144], v, sizeof v);
 
     if (cudaMalloc(&ctx->d_tables, host.size() * sizeof(u64)) != cudaSuccess) return fail(GF2X_ENOMEM);
-    if (cudaMalloc(&ctx->d_status, kAlign) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_state, kStateBytes) != cudaSuccess) {
         cudaFree(ctx->d_tables);
         return fail(GF2X_ENOMEM);
     }
-    ctx->d_sync = (GridSync *)((char *)ctx->d_status + 128);
-    ctx->d_word = (unsigned long long *)((char *)ctx->d_status + 192);
+    ctx->d_status = (int *)ctx->d_state;
+    ctx->d_sync = (GridSync *)((char *)ctx->d_state + 128);
+    ctx->d_word = (unsigned long long *)((char *)ctx->d_state + 192);
     ctx->d_cvt = ctx->d_tables;
     ctx->d_enc = ctx->d_tables + 2048;
     ctx->d_dec = ctx->d_tables + 4096;
@@ -841,12 +847,12 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     std::vector<u64> host128(gf2x::kTables128Words);
     if (!gf2x::m128_build_tables(host128.data())) {
         cudaFree(ctx->d_tables);
-        cudaFree(ctx->d_status);
+        cudaFree(ctx->d_state);
         return fail(GF2X_EINVAL);
     }
     if (cudaMalloc(&ctx->d_tables128, host128.size() * sizeof(u64)) != cudaSuccess) {
         cudaFree(ctx->d_tables);
-        cudaFree(ctx->d_status);
+        cudaFree(ctx->d_state);
         return fail(GF2X_ENOMEM);
     }
     ctx->d_cvt128 = ctx->d_tables128;
@@ -856,10 +862,10 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     if (cudaMemcpy(ctx->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_tables128, host128.data(), host128.size() * sizeof(u64), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, kAlign) != cudaSuccess) {
+        cudaMemset(ctx->d_state, 0, kStateBytes) != cudaSuccess) {
         cudaFree(ctx->d_tables);
         cudaFree(ctx->d_tables128);
-        cudaFree(ctx->d_status);
+        cudaFree(ctx->d_state);
         return fail(GF2X_ECUDA);
     }
     *out = ctx;
@@ -891,7 +897,7 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx)
     gf2x::tuner_destroy(ctx->tuner);
     cudaFree(ctx->d_tables);
     cudaFree(ctx->d_tables128);
-    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_state);
     delete ctx;
 }
 
@@ -951,12 +957,13 @@ static_assert(GF2X_KNOB_UNIT16_R == gf2x::TUNE_UNIT16_R && GF2X_KNOB_BOTTOM_SHAP
                   GF2X_KNOB_WINDOW_DEPTH == gf2x::TUNE_WINDOW_DEPTH &&
                   GF2X_KNOB_M128_BOTTOM_CHUNK == gf2x::TUNE_M128_BOTTOM_CHUNK &&
                   GF2X_KNOB_BOTTOM_DEPTH == gf2x::TUNE_BFLY_DEPTH &&
-                  GF2X_KNOB_M128_BOTTOM_DEPTH == gf2x::TUNE_M128_BFLY_DEPTH,
+                  GF2X_KNOB_M128_BOTTOM_DEPTH == gf2x::TUNE_M128_BFLY_DEPTH &&
+                  GF2X_KNOB_BATCH_PERSISTENT == gf2x::TUNE_BATCH_PERSIST,
               "the ABI's knob numbers are the tuner's");
 
 gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice)
 {
-    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_M128_BOTTOM_DEPTH || choice < -1) return GF2X_EINVAL;
+    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_BATCH_PERSISTENT || choice < -1) return GF2X_EINVAL;
     gf2x::tuner_pin(ctx->tuner, knob, choice);
     ++graphs(ctx)->gen;           // captured graphs keep their shapes: capture again
     return GF2X_OK;
@@ -1263,6 +1270,13 @@ gf2x_status gf2x_selftest_wait_timeout(gf2x_ctx *ctx, void *stream)
     return from_cuda(gf2x::wait_timeout_probe(ctx, ctx->d_sync, (cudaStream_t)stream));
 }
 
+gf2x_status gf2x_selftest_queue_timeout(gf2x_ctx *ctx, void *stream)
+{
+    if (!ctx) return GF2X_EINVAL;
+    DeviceGuard g(ctx->device);
+    return from_cuda(gf2x::persist_selftest_timeout(ctx, (cudaStream_t)stream, 20000000ull));   // 20 ms
+}
+
 size_t gf2x_batch_workspace_bytes(const gf2x_job *jobs, size_t count)
 {
     if (!jobs && count) return 0;
@@ -1288,7 +1302,39 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
     // the job table goes to the device before the kernels (every call)
     TRY(cudaMemcpyAsync(ws, bp.table.data(), bp.table.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
     const std::vector<ClassRun> runs = bind_runs(bp, ws);
+    // One persistent launch (persist.cu) unless the knob asks for class launches or a class
+    // needs a launch shape the persistent kernel does not have: record every class's
+    // launches, upload the plan, and the launch itself is what runs (and is captured).
+    static const int modes[2] = {0, 1};
+    bool persistent = gf2x::tune_pinned(ctx, gf2x::TUNE_BATCH_PERSIST, modes, 2, 1) == 1;
+    gf2x::PersistLaunch pl{};
+    u64 plan_digest = 0;
+    if (persistent) {
+        std::vector<Recorder> recs(runs.size());
+        std::vector<const Recorder *> rp;
+        for (size_t c = 0; c < runs.size() && persistent; ++c) {
+            recs[c].jobs = runs[c].count;
+            ctx->rec = &recs[c];
+            const gf2x_status rs = run_class(ctx, runs[c], st);
+            ctx->rec = nullptr;
+            persistent = rs == GF2X_OK && gf2x::persist_supported(recs[c]);
+            rp.push_back(&recs[c]);
+        }
+        if (persistent) {
+            const int saved = ctx->stage;
+            ctx->stage = STAGE_PERSIST;
+            const cudaError_t pe = gf2x::persist_prepare(ctx, rp.data(), (int)rp.size(), (char *)ws + bp.persist_off,
+                                                         bp.persist_bytes, st, &pl);
+            ctx->stage = saved;
+            if (pe != cudaSuccess) return GF2X_ECUDA;
+            plan_digest = pl.digest;
+        }
+    }
     auto run_all = [&](cudaStream_t s2) -> gf2x_status {
+        if (persistent) {
+            StageScope sc(ctx, STAGE_PERSIST, s2);
+            return from_cuda(gf2x::persist_launch(ctx, pl, s2));
+        }
         for (const ClassRun &r : runs) {
             gf2x_status e = run_class(ctx, r, s2);
             if (e != GF2X_OK) return e;
@@ -1303,7 +1349,7 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         return run_all(st);
     const u64 key = hash_table(bp.table, ws);
     for (BatchGraph &e : bc->entries)
-        if (e.key.same(key, ws, bp.table) && e.profiling == ctx->profiling && e.gen == gc->gen) {
+        if (e.key.same(key, ws, bp.table, plan_digest) && e.profiling == ctx->profiling && e.gen == gc->gen) {
             e.stamp = ++gc->clock;
             TRY(cudaGraphLaunch(e.exec, st));
             for (int k = 0; k < STAGE_COUNT; ++k) ctx->launches[k] += e.launches[k];
@@ -1313,19 +1359,19 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
         }
     bool repeat = false;
     for (size_t k = 0; k < bc->seen.size(); ++k)
-        if (bc->seen[k].same(key, ws, bp.table)) {
+        if (bc->seen[k].same(key, ws, bp.table, plan_digest)) {
             repeat = true;
             bc->seen.erase(bc->seen.begin() + (long)k);
             break;
         }
     if (!repeat) {
         if (bc->seen.size() >= 32) bc->seen.erase(bc->seen.begin());
-        bc->seen.push_back(BatchKey{key, ws, bp.table});
+        bc->seen.push_back(BatchKey{key, ws, bp.table, plan_digest});
         return run_all(st);
     }
     if (!gc->cap && cudaStreamCreateWithFlags(&gc->cap, cudaStreamNonBlocking) != cudaSuccess) return run_all(st);
     BatchGraph e{};
-    e.key = BatchKey{key, ws, bp.table};
+    e.key = BatchKey{key, ws, bp.table, plan_digest};
     e.profiling = ctx->profiling;
     unsigned long long before[STAGE_COUNT];
     for (int k = 0; k < STAGE_COUNT; ++k) before[k] = ctx->launches[k];
@@ -1391,7 +1437,8 @@ extern "C" {
 const char *gf2x_stage_name(int stage)
 {
     static const char *names[STAGE_COUNT] = {"load", "basis_cvt", "encode", "butterfly", "pointwise",
-                                             "ibutterfly", "decode", "ibasis_cvt", "store", "bottom_fused"};
+                                             "ibutterfly", "decode", "ibasis_cvt", "store", "bottom_fused",
+                                             "persistent_batch"};
     return (stage >= 0 && stage < STAGE_COUNT) ? names[stage] : "unknown";
 }
 

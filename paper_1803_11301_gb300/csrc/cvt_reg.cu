@@ -1,395 +1,24 @@
-// Register-resident parts of BasisCvt / iBasisCvt (Alg. 1, Sec. 2.3.1).
-//
-// (1) The conversion of every aligned 2^16-bit block on its own.  For a
-// length 2^K with 16 <= K <= 32, Alg. 1 splits at tau = 2^16 (the largest 2^i
-// with i a power of two and i <= K - 1), so its last part is the same
-// algorithm inside every block of 2^16 bits; for K >= 33 it splits at 2^32
-// and the 2^32-bit blocks again end with it.  Its step list, the flattening
-// described in cvt.cu, is fixed: 32 (h, d) steps, generated below at compile
-// time.  One warp per block: lane L holds the 32 consecutive words 32L ..
-// 32L+31 (2048 bits).  A step whose segments fit in 2048 bits runs inside
-// every lane with fixed register indices; a wider step (h >= 2^11, 15 of the
-// 32) pairs lane L of the lower half of a segment with lane L + h/2048 of the
-// upper half and moves the words it needs with warp shuffles.  No barrier is
-// taken between steps; shared memory only turns the coalesced load (lane L
-// gets words L, L+32, ...) into the per-lane layout and back, with an XOR
-// swizzle that keeps both sides free of bank conflicts.
-//
-// (2) The "outer" conversion of Alg. 1 on whole units: BasisCvt of length
-// 2^M whose coefficients are units of U words (the outer step of a split at
-// tau = U bits).  Every step then moves whole units, lo[q] ^= hi'[q - D], so
-// each of the U word columns is an independent BasisCvt of 2^M words.  A lane
-// group of min(2^M, 32) lanes holds one column, 2^M / 32 units per lane, and
-// runs the compile-time step list of BasisCvt(2^M) with the same
-// register/shuffle scheme as (1), here without bit shifts.
-#include "gf2x_common.cuh"
+// Register-resident parts of BasisCvt / iBasisCvt (Alg. 1, Sec. 2.3.1): launches of
+// the 2^16-bit block kernel and the outer-conversion kernel, whose bodies and
+// method are in cvt_reg_dev.cuh.
+#include "cvt_reg_dev.cuh"
 
 namespace gf2x {
 namespace {
+using namespace cvtrk;
 
-constexpr int kUnitWords = 1024;        // 2^16 bits
-
-struct StepList {
-    int n;
-    signed char lh[40], ld[40];         // log2 h, log2 d (bits)
-};
-
-// Same recursion as the host planner: Taylor steps at s_i = x^tau + x, then
-// the outer conversion (unit tau), then the inner one (unit 1).
-constexpr void gen_steps(StepList &s, int K, int ulog)
-{
-    if (K <= 1) return;
-    int i = 1;
-    while (2 * i <= K - 1) i *= 2;
-    for (int k = K - i - 1; k >= 0; --k) {
-        s.lh[s.n] = (signed char)(i + k + ulog);
-        s.ld[s.n] = (signed char)(k + ulog);
-        ++s.n;
-    }
-    gen_steps(s, K - i, ulog + i);
-    gen_steps(s, i, ulog);
-}
-
-constexpr StepList make_steps(int K)
-{
-    StepList s{};
-    gen_steps(s, K, 0);
-    return s;
-}
-
-constexpr StepList kSteps16 = make_steps(16);
-static_assert(kSteps16.n == 32, "BasisCvt of 2^16 bits has 32 steps");
-
-template <int M>
-struct StepsOf {
-    static constexpr StepList list = make_steps(M);
-};
-
-constexpr u64 seg_mask(int h, int lo_bit, int hi_bit)
-{
-    // bits [lo_bit, hi_bit) of every 2h-bit segment of a word (h < 64)
-    u64 one = ((1ull << (hi_bit - lo_bit)) - 1) << lo_bit;
-    u64 m = 0;
-    for (int s = 0; s < 64; s += 2 * h) m |= one << s;
-    return m;
-}
-
-__device__ __forceinline__ u64 shfl(u64 v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-// One step of a conversion whose elements are whole words (h = H = 2^LH and
-// d = D = 2^LD elements), on a column held by a group of lanes with R
-// consecutive elements per lane; gl is the lane's index in its group.
-// Forward: hi' = hi with its quotient fix hi[r] ^= hi[H - D + r] (r < D),
-// then lo[q] ^= hi'[q - D].  Inverse: the lo update with the current hi, then
-// the fix.
-template <int R, int LH, int LD, bool INV>
-__device__ __forceinline__ void wstep(u64 (&w)[R], int gl, int lane)
-{
-    constexpr int H = 1 << LH, D = 1 << LD;
-    if constexpr (2 * H <= R) {
-        // segments inside one lane
-#pragma unroll
-        for (int b = 0; b < R; b += 2 * H) {
-            if (!INV) {
-#pragma unroll
-                for (int r = 0; r < D; ++r) w[b + H + r] ^= w[b + 2 * H - D + r];
-            }
-#pragma unroll
-            for (int q = D; q < H; ++q) w[b + q] ^= w[b + H + q - D];
-            if (INV) {
-#pragma unroll
-                for (int r = 0; r < D; ++r) w[b + H + r] ^= w[b + 2 * H - D + r];
-            }
-        }
-    } else {
-        // segments of 2P lanes: lane s < P of a segment holds lo elements,
-        // lane s >= P the hi elements at the same offsets
-        constexpr int P = H / R;
-        const int s = gl & (2 * P - 1);
-        const int base = lane - s;
-        const u64 lo_mask = s < P ? ~0ull : 0ull;
-        if constexpr (D < R) {
-            // hi[r] ^= hi[H - D + r] for r < D: first hi lane, from the last one
-            auto fix = [&]() {
-#pragma unroll
-                for (int r = 0; r < D; ++r) {
-                    const u64 t = shfl(w[R - D + r], base + 2 * P - 1);
-                    if (s == P) w[r] ^= t;
-                }
-            };
-            if (!INV) fix();
-            // element j of lo lane s takes element j - D of hi lane s (or
-            // element R + j - D of hi lane s - 1)
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                u64 v;
-                if (j >= D) {
-                    v = shfl(w[j - D], lane + P);
-                } else {
-                    v = shfl(w[R + j - D], lane + P - 1);
-                    if (s == 0) v = 0;
-                }
-                w[j] ^= v & lo_mask;
-            }
-            if (INV) fix();
-        } else {
-            // whole lanes: DL = D/R.  Lo lane s >= DL takes hi lane s - DL
-            // (lane + P - DL); hi lane s < P + DL is fixed from lane + P - DL.
-            constexpr int DL = D / R;
-            const u64 fix_mask = (s >= P && s < P + DL) ? ~0ull : 0ull;
-            const u64 lo_take = (s >= DL && s < P) ? ~0ull : 0ull;
-            if (!INV) {
-#pragma unroll
-                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & fix_mask;
-#pragma unroll
-                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & lo_take;
-            } else {
-                // sources of both updates are unfixed hi lanes
-#pragma unroll
-                for (int j = 0; j < R; ++j) w[j] ^= shfl(w[j], lane + P - DL) & (fix_mask | lo_take);
-            }
-        }
-    }
-}
-
-// Word index p of a 2^16-bit block -> its slot in shared memory: word 32a + b
-// at 32a + (b ^ a).  Lanes that hold R consecutive words each (R = 8, 16 or
-// 32) and read or write their j-th word together hit 16 bank pairs, two lanes
-// each; so do 32 lanes that take 32 consecutive words.
-__device__ __forceinline__ int unit_slot(int p) { return (p & ~31) | ((p & 31) ^ ((p >> 5) & 31)); }
-
-// A step whose segments span several warps, through shared memory: every
-// thread stores its words, then takes what it needs from that snapshot
-// (forward: lo[q] ^= hi'[q - dw], hi' = hi with the quotient fix; inverse: the
-// lo update with the snapshot hi; both: the fix of hi[r] for r < dw).
-template <int R, int LH, int LD, bool INV>
-__device__ __forceinline__ void xstep(u64 (&w)[R], int t, u64 *sm)
-{
-    constexpr int hw = 1 << (LH - 6);
-    __syncthreads();                                    // the previous readers of sm are done
-#pragma unroll
-    for (int j = 0; j < R; ++j) sm[unit_slot(t * R + j)] = w[j];
-    __syncthreads();
-    const int p0 = t * R;
-    const int q0 = p0 & (2 * hw - 1);                   // offset in the segment; all R words in one half
-    const int sb = p0 - q0;
-    auto at = [&](int x) { return sm[unit_slot(sb + x)]; };
-    if (q0 < hw) {
-        if constexpr (LD >= 6) {
-            constexpr int dw = 1 << (LD - 6);
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int q = q0 + j;
-                if (q < dw) continue;
-                const int x = q - dw;
-                u64 v = at(hw + x);
-                if (!INV && x < dw) v ^= at(2 * hw - dw + x);
-                w[j] ^= v;
-            }
-        } else {
-            constexpr int d = 1 << LD;
-            const u64 fix0 = INV ? 0 : at(2 * hw - 1) >> (64 - d);   // hi'[0] = hi[0] ^ fix0
-            u64 prev = q0 > 0 ? at(hw + q0 - 1) : 0;
-            if (q0 == 1) prev ^= fix0;
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                u64 v = at(hw + q0 + j);
-                if (q0 + j == 0) v ^= fix0;
-                w[j] ^= (v << d) | (prev >> (64 - d));
-                prev = v;
-            }
-        }
-    } else {
-        const int r0 = q0 - hw;
-        if constexpr (LD >= 6) {
-            constexpr int dw = 1 << (LD - 6);
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                if (r0 + j < dw) w[j] ^= at(2 * hw - dw + r0 + j);
-        } else {
-            constexpr int d = 1 << LD;
-            if (r0 == 0) w[0] ^= at(2 * hw - 1) >> (64 - d);
-        }
-    }
-}
-
-// One step (h = 2^LH, d = 2^LD bits) on a 2^16-bit block held by 1024/R
-// threads, R consecutive words each (thread t: words tR .. tR + R - 1).
-// Forward: hi' = hi with its quotient fix, lo ^= (hi' << d) mod x^h.
-// Inverse: lo ^= (hi << d) mod x^h with the current hi, then the fix.
-// Steps with d >= 64 bits move whole words (wstep); wider than a warp: xstep.
-template <int R, int LH, int LD, bool INV>
-__device__ __forceinline__ void step(u64 (&w)[R], int t, int lane, u64 *sm)
-{
-    if constexpr (LH >= 6 && (2 << (LH - 6)) > 32 * R) {
-        xstep<R, LH, LD, INV>(w, t, sm);
-    } else if constexpr (LD >= 6) {
-        wstep<R, LH - 6, LD - 6, INV>(w, lane, lane);
-    } else if constexpr (LH < 6) {
-        // segments inside one word
-        constexpr int h = 1 << LH, d = 1 << LD, sh = h - d;
-        constexpr u64 ma = seg_mask(h, h, h + d);      // bottom d bits of hi
-        constexpr u64 mb = seg_mask(h, d, h);          // lo bits [d, h)
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            u64 x = w[j];
-            if (!INV) {
-                x ^= (x >> sh) & ma;
-                x ^= (x >> sh) & mb;
-            } else {
-                x ^= (x >> sh) & mb;
-                x ^= (x >> sh) & ma;
-            }
-            w[j] = x;
-        }
-    } else if constexpr ((2 << (LH - 6)) <= R) {
-        // segments of 2hw <= R words inside one lane; d < 64 bits
-        constexpr int hw = 1 << (LH - 6), d = 1 << LD;
-#pragma unroll
-        for (int b = 0; b < R; b += 2 * hw) {
-            if (!INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
-#pragma unroll
-            for (int q = hw - 1; q >= 0; --q) {
-                u64 t2 = w[b + hw + q] << d;
-                if (q > 0) t2 |= w[b + hw + q - 1] >> (64 - d);
-                w[b + q] ^= t2;
-            }
-            if (INV) w[b + hw] ^= w[b + 2 * hw - 1] >> (64 - d);
-        }
-    } else {
-        // segments of 2P lanes (lane s < P of a segment holds lo words, lane
-        // s >= P the hi words at the same offsets); d < 64 bits
-        constexpr int P = (1 << (LH - 6)) / R, d = 1 << LD;
-        const int s = lane & (2 * P - 1);
-        const int base = lane - s;
-        const u64 lo_mask = s < P ? ~0ull : 0ull;
-        // the fix: hi[0] ^= hi[hw-1] >> (64 - d), on the first hi lane
-        auto fix = [&]() {
-            const u64 top = shfl(w[R - 1], base + 2 * P - 1);
-            if (s == P) w[0] ^= top >> (64 - d);
-        };
-        if (!INV) fix();
-        // lo[q] ^= (hi[q] << d) | (hi[q-1] >> (64 - d))
-        u64 prev = shfl(w[R - 1], lane + P - 1);
-        if (s == 0) prev = 0;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const u64 v = shfl(w[j], lane + P);
-            w[j] ^= ((v << d) | (prev >> (64 - d))) & lo_mask;
-            prev = v;
-        }
-        if (INV) fix();
-    }
-}
-
-template <int R, bool INV, int I>
-__device__ __forceinline__ void run_steps(u64 (&w)[R], int t, int lane, u64 *sm)
-{
-    if constexpr (I < 32) {
-        // forward order, or the reversed list for the inverse
-        constexpr int k = INV ? 31 - I : I;
-        step<R, kSteps16.lh[k], kSteps16.ld[k], INV>(w, t, lane, sm);
-        run_steps<R, INV, I + 1>(w, t, lane, sm);
-    }
-}
-
-// One block of 1024/R threads per 2^16-bit block; blockIdx.y is the job of a
-// batch.  Words go through shared memory in both directions so that global
-// accesses are coalesced (thread t takes words t, t + 1024/R, ...).
 template <bool INV, int R>
 __global__ void __launch_bounds__(1024 / R) k_cvt_unit16(u64 *bits, u64 stride)
 {
-    constexpr int NT = 1024 / R;
     __shared__ u64 sm[kUnitWords];
-    const int t = threadIdx.x, lane = t & 31;
-    u64 *g = bits + (u64)blockIdx.y * stride + (u64)blockIdx.x * kUnitWords;
-#pragma unroll 8
-    for (int i = 0; i < R; ++i) sm[unit_slot(NT * i + t)] = g[NT * i + t];
-    __syncthreads();
-    u64 w[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) w[j] = sm[unit_slot(t * R + j)];
-    run_steps<R, INV, 0>(w, t, lane, sm);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < R; ++j) sm[unit_slot(t * R + j)] = w[j];
-    __syncthreads();
-#pragma unroll 8
-    for (int i = 0; i < R; ++i) g[NT * i + t] = sm[unit_slot(NT * i + t)];
+    cvt_unit16_body<INV, R>(launch_block(), sm, bits, stride);
 }
 
-template <int M, bool INV, int I>
-__device__ __forceinline__ void run_outer_steps(u64 (&w)[(1 << M) >= 32 ? (1 << M) / 32 : 1], int gl, int lane)
-{
-    constexpr StepList S = StepsOf<M>::list;
-    if constexpr (I < S.n) {
-        constexpr int k = INV ? S.n - 1 - I : I;
-        wstep<((1 << M) >= 32 ? (1 << M) / 32 : 1), S.lh[k], S.ld[k], INV>(w, gl, lane);
-        run_outer_steps<M, INV, I + 1>(w, gl, lane);
-    }
-}
-
-// Block shape of the outer kernel: 16 warps (8 for M = 9, whose 16 units per
-// lane take more registers), one column per warp for M >= 5.
-template <int M>
-struct OuterShape {
-    static constexpr int NU = 1 << M;                   // units per column
-    static constexpr int LPC = NU < 32 ? NU : 32;       // lanes per column
-    static constexpr int R = NU / LPC;                  // units per lane
-    static constexpr int CPW = 32 / LPC;                // columns per warp
-    static constexpr int WARPS = M >= 9 ? 8 : 16;
-    static constexpr int THREADS = WARPS * 32;
-    static constexpr int CW = WARPS * CPW;              // columns per block
-    static constexpr int S = NU + 1;                    // shared-memory column stride (odd)
-    // lanes of a column hold units gl R .. gl R + R - 1; unit j of lane gl sits
-    // at gl R + (j ^ sigma(gl)), so the 32 lanes reading their j-th unit hit
-    // 16 different bank pairs (two lanes each)
-    static __device__ __forceinline__ int slot(int gl, int j)
-    {
-        constexpr int spread = R >= 16 ? 1 : 16 / R;
-        return gl * R + (j ^ ((gl / spread) & (R - 1)));
-    }
-};
-
-// Outer BasisCvt(2^M) on units of 2^ulog words: unit r, column c of chunk ch
-// is word (ch 2^M + r) 2^ulog + c.  A block takes CW adjacent columns: their
-// unit rows are staged through shared memory (coalesced 8-byte cp.async, one
-// row segment of CW words per unit), each lane group takes one column into
-// registers, runs the steps, and the rows go back the same way.
 template <int M, bool INV>
 __global__ void __launch_bounds__(OuterShape<M>::THREADS) k_cvt_outer(u64 *bits, const u64 *src, int ulog, u64 stride)
 {
-    using Sh = OuterShape<M>;
-    constexpr int NU = Sh::NU, LPC = Sh::LPC, R = Sh::R, CW = Sh::CW, S = Sh::S;
-    __shared__ u64 st[CW * S];
-    const u64 col0 = (u64)blockIdx.x * CW;
-    const u64 ch = col0 >> ulog, c0 = col0 & ((1ull << ulog) - 1);
-    const u64 off = (u64)blockIdx.y * stride + ((ch << M) << ulog) + c0;
-    u64 *g = bits + off;
-    const u64 *gs = src + off;
-    // rows in: element (unit r, column w) -> st[w S + slot(r / R, r % R)]
-    for (int e = threadIdx.x; e < NU * CW; e += Sh::THREADS) {
-        const int r = e / CW, w = e % CW;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(st + w * S + Sh::slot(r / R, r % R));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gs + ((u64)r << ulog) + w)
-                     : "memory");
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (LPC - 1);
-    const int w0 = (threadIdx.x >> 5) * Sh::CPW + lane / LPC;   // this lane group's column
-    u64 w[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) w[j] = st[w0 * S + Sh::slot(gl, j)];
-    run_outer_steps<M, INV, 0>(w, gl, lane);
-#pragma unroll
-    for (int j = 0; j < R; ++j) st[w0 * S + Sh::slot(gl, j)] = w[j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < NU * CW; e += Sh::THREADS) {
-        const int r = e / CW, w = e % CW;
-        g[((u64)r << ulog) + w] = st[w * S + Sh::slot(r / R, r % R)];
-    }
+    __shared__ u64 st[OuterShape<M>::SMEM_WORDS];
+    cvt_outer_body<M, INV>(launch_block(), st, bits, src, ulog, stride);
 }
 
 template <int M>
@@ -430,6 +59,22 @@ cudaError_t basis_cvt_outer(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L, int
     // every block's columns lie in one chunk: CW divides the unit
     if (cw == 0 || ulog < 0 || (1ull << ulog) % (u64)cw != 0 || (columns >> ulog) << ulog != columns)
         return cudaErrorInvalidValue;
+    if (recording(ctx)) {
+        // blocks of 8 warps, the persistent kernel's block size
+        static const int kColsOf[10] = {0, 0, OuterShape<2, 8>::CW, OuterShape<3, 8>::CW, OuterShape<4, 8>::CW,
+                                        OuterShape<5, 8>::CW, OuterShape<6, 8>::CW, OuterShape<7, 8>::CW,
+                                        OuterShape<8, 8>::CW, OuterShape<9, 8>::CW};
+        static const int kWordsOf[10] = {0, 0, OuterShape<2, 8>::SMEM_WORDS, OuterShape<3, 8>::SMEM_WORDS,
+                                         OuterShape<4, 8>::SMEM_WORDS, OuterShape<5, 8>::SMEM_WORDS,
+                                         OuterShape<6, 8>::SMEM_WORDS, OuterShape<7, 8>::SMEM_WORDS,
+                                         OuterShape<8, 8>::SMEM_WORDS, OuterShape<9, 8>::SMEM_WORDS};
+        const u64 cw8 = (u64)kColsOf[M];
+        if ((1ull << ulog) % cw8 != 0) return cudaErrorInvalidValue;
+        const unsigned gx = (unsigned)(columns / cw8);
+        SegRec r{SEG_OUTER, {M, inverse ? 1 : 0, ulog, 0}, gx, (unsigned)count, 256u, (unsigned)kWordsOf[M] * 8, gx,
+                 -1, {(u64)bits, (u64)src, stride}};
+        return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+    }
     switch (M) {
     case 2: launch_outer<2>(bits, src, ulog, columns, inverse, count, stride, st); break;
     case 3: launch_outer<3>(bits, src, ulog, columns, inverse, count, stride, st); break;
@@ -454,6 +99,11 @@ cudaError_t basis_cvt_unit16_r(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, in
     const u64 units = L >> 16;
     if (units == 0) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)units, (unsigned)count);
+    if (recording(ctx)) {
+        SegRec r{SEG_UNIT16, {R, inverse ? 1 : 0, 0, 0}, grid.x, grid.y, (unsigned)(1024 / R), kUnitWords * 8, grid.x, -1,
+                 {(u64)bits, stride}};
+        return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+    }
     switch (R * 2 + (inverse ? 1 : 0)) {
     case 16: k_cvt_unit16<false, 8><<<grid, 128, 0, st>>>(bits, stride); break;
     case 17: k_cvt_unit16<true, 8><<<grid, 128, 0, st>>>(bits, stride); break;
@@ -476,7 +126,8 @@ cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int 
     const u64 blocks = (L >> 16) * (u64)count;
     int R = blocks <= 4 * (u64)ctx->num_sms ? 8 : 32;
     static const int cands[3] = {8, 16, 32};
-    if (!scratch) R = tune_pinned(ctx, TUNE_UNIT16_R, cands, 3, R);
+    if (recording(ctx)) R = 8;               // the shape a block of the persistent kernel runs
+    else if (!scratch) R = tune_pinned(ctx, TUNE_UNIT16_R, cands, 3, R);
     else {
         R = tune_choice(ctx, TUNE_UNIT16_R, (tune_bucket(blocks) << 1) | (inverse ? 1u : 0u), cands, 3, R,
                         [&](int r) { return basis_cvt_unit16_r(ctx, scratch, L, inverse, count, stride, r, st); }, st);

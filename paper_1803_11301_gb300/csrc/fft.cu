@@ -1,143 +1,52 @@
 // Encode / Decode (Alg. 4), the pointwise product of Alg. 5 and the
 // bit-array load/store around them.
-#include "gf2x_common.cuh"
+#include "fft_dev.cuh"
 
 namespace gf2x {
 namespace {
-
-constexpr int kCols = 32;            // word columns per Encode/Decode block
-
-// Copy a 16 KiB window table (16-byte aligned: it sits in the context's
-// cudaMalloc'd table block) to shared memory with asynchronous 16-byte copies;
-// the caller waits (cp.async.wait_all) and synchronises.
-__device__ __forceinline__ void load_table_async(u64 *dst, const u64 *__restrict__ src)
-{
-    for (int k = 2 * threadIdx.x; k < 8 * 256; k += 2 * blockDim.x)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst + k)),
-                     "l"(src + k)
-                     : "memory");
-}
-
-__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// ------------------------------------------------------------------- Encode
-// n_p = 2^l >= 64.  Row j of the novelpoly bit array is bits [j n_p, (j+1) n_p),
-// i.e. RW = n_p/64 words.  For the 64 points i in word column w, the 64 words
-// (row j, column w) form a 64x64 bit matrix whose transpose gives, per i, the
-// vector (a_{j n_p + i})_j; f_i = that vector times R (Alg. 4).
-//
-// A block stages 64 rows x 32 word columns in shared memory (coalesced row
-// reads); each warp transposes one column's 64x64 bit matrix with shuffles
-// (Sec. 4.4's block-swap transpose: a 32-bit half swap in registers, then
-// five exchange rounds across lanes) and applies R through 8-bit window tables
-// loaded once per block.  Rows at or above `rows` are zero and are not read.
-constexpr int kPad = kCols + 1;      // padded row of the staging tile
+using namespace fftk;
 
 __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u64 rw, int rows,
                                                 const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups, u64 stride,
                                                 u64 out_stride)
 {
-    novel += (u64)blockIdx.y * stride;            // job of a batch
-    f += (u64)blockIdx.y * out_stride;
     __shared__ __align__(16) u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
-    const int cols = rw < kCols ? (int)rw : kCols;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    pdl_allow();
-    load_table_async(tab, enc);                   // in flight with the first tile's loads
-    pdl_wait();
-    for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
-        const u64 w0 = g * cols;
-        __syncthreads();
-        for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
-            const int j = k / cols, w = k % cols;
-            tile[j * kPad + w] = j < rows ? novel[(u64)j * rw + w0 + w] : 0;
-        }
-        copy_async_wait();
-        __syncthreads();
-        for (int w = warp; w < cols; w += blockDim.x >> 5) {
-            u64 A = tile[lane * kPad + w], B = tile[(lane + 32) * kPad + w];
-            transpose64(A, B, lane);
-            const u64 base = (w0 + w) * 64;
-            f[base + lane] = lin64(tab, A);
-            f[base + lane + 32] = lin64(tab, B);
-        }
-    }
+    encode_body(launch_block(), tab, tile, novel, rw, rows, enc, f, groups, stride, out_stride);
 }
 
-// n_p < 64: the whole transform is at most 32 words; one block, bit by bit.
-// Bits at or above nonzero_bits are zero and are not read.
 __global__ void k_encode_small(const u64 *__restrict__ novel, int l, u64 nonzero_bits, const u64 *__restrict__ enc,
                                u64 *__restrict__ f, u64 stride, u64 out_stride)
 {
-    novel += (u64)blockIdx.y * stride;
-    f += (u64)blockIdx.y * out_stride;
-    const u64 np = 1ull << l;
-    for (u64 i = threadIdx.x; i < np; i += blockDim.x) {
-        u64 u = 0;
-        for (int j = 0; j < 64; ++j) {
-            u64 pos = (u64)j * np + i;
-            if (pos < nonzero_bits) u |= ((novel[pos >> 6] >> (pos & 63)) & 1ull) << j;
-        }
-        f[i] = lin64(enc, u);
-    }
+    encode_small_body(launch_block(), novel, l, nonzero_bits, enc, f, stride, out_stride);
 }
 
-// ------------------------------------------------------------------- Decode
-// The inverse of Encode: per point, the bits (c_{j n_p + i})_j = h_i R^{-1};
-// a warp transposes the 64 vectors of one word column back into 64 row words.
 __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 rw, const u64 *__restrict__ dec,
                                                 u64 *__restrict__ novel, u64 groups, u64 stride)
 {
-    h += (u64)blockIdx.y * stride;
-    novel += (u64)blockIdx.y * stride;
     __shared__ __align__(16) u64 tab[8 * 256];
     __shared__ u64 tile[64 * kPad];
-    const int cols = rw < kCols ? (int)rw : kCols;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    pdl_allow();
-    load_table_async(tab, dec);
-    copy_async_wait();
-    __syncthreads();
-    pdl_wait();
-    for (u64 g = blockIdx.x; g < groups; g += gridDim.x) {
-        const u64 w0 = g * cols;
-        for (int w = warp; w < cols; w += blockDim.x >> 5) {
-            const u64 base = (w0 + w) * 64;
-            u64 A = lin64(tab, h[base + lane]), B = lin64(tab, h[base + lane + 32]);
-            transpose64(A, B, lane);
-            tile[lane * kPad + w] = A;
-            tile[(lane + 32) * kPad + w] = B;
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < 64 * cols; k += blockDim.x) {
-            const int j = k / cols, w = k % cols;
-            novel[(u64)j * rw + w0 + w] = tile[j * kPad + w];
-        }
-        __syncthreads();
-    }
+    decode_body(launch_block(), tab, tile, h, rw, dec, novel, groups, stride);
 }
 
 __global__ void k_decode_small(const u64 *__restrict__ h, int l, const u64 *__restrict__ dec, u64 *__restrict__ novel,
                                u64 stride)
 {
-    h += (u64)blockIdx.y * stride;
-    novel += (u64)blockIdx.y * stride;
     __shared__ u64 vec[64];
-    const u64 np = 1ull << l;
-    for (u64 i = threadIdx.x; i < np; i += blockDim.x) vec[i] = lin64(dec, h[i]);
-    __syncthreads();
-    const u64 words = np;                        // n/64 = n_p words
-    for (u64 wd = threadIdx.x; wd < words; wd += blockDim.x) {
-        u64 out = 0;
-        for (int b = 0; b < 64; ++b) {
-            u64 pos = wd * 64 + b;
-            u64 j = pos >> l, i = pos & (np - 1);
-            out |= ((vec[i] >> j) & 1ull) << b;
-        }
-        novel[wd] = out;
-    }
+    decode_small_body(launch_block(), vec, h, l, dec, novel, stride);
 }
+
+__global__ void k_load_jobs(const JobDev *__restrict__ jobs, int which, u64 *__restrict__ dst, u64 stride,
+                            u64 dst_words)
+{
+    load_jobs_body(launch_block(), jobs, which, dst, stride, dst_words);
+}
+
+__global__ void k_store_jobs(const u64 *__restrict__ src, u64 stride, const JobDev *__restrict__ jobs)
+{
+    store_jobs_body(launch_block(), src, stride, jobs);
+}
+
 
 __global__ void k_pointwise(const u64 *__restrict__ a, const u64 *__restrict__ b, u64 *c, u64 count)
 {
@@ -244,39 +153,6 @@ __global__ void k_load_pair(const u64 *__restrict__ a, u64 na, const u64 *__rest
     dst[w] = v;
 }
 
-// Batch forms: job j of the launch (blockIdx.y) reads operand `which` of
-// jobs[j] into dst + j * stride, or writes its product from src + j * stride.
-__global__ void k_load_jobs(const JobDev *__restrict__ jobs, int which, u64 *__restrict__ dst, u64 stride,
-                            u64 dst_words)
-{
-    const JobDev jb = jobs[blockIdx.y];
-    const u64 *src = which ? jb.b : jb.a;
-    const u64 nbits = which ? jb.nb : jb.na;
-    dst += (u64)blockIdx.y * stride;
-    for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < dst_words; w += (u64)gridDim.x * blockDim.x) {
-        const u64 nw = (nbits + 63) >> 6;
-        u64 v = 0;
-        if (w < nw) {
-            v = src[w];
-            if (w == nw - 1 && (nbits & 63)) v &= (~0ull) >> (64 - (nbits & 63));
-        }
-        dst[w] = v;
-    }
-}
-
-__global__ void k_store_jobs(const u64 *__restrict__ src, u64 stride, const JobDev *__restrict__ jobs)
-{
-    const JobDev jb = jobs[blockIdx.y];
-    const u64 nc = (jb.na && jb.nb) ? jb.na + jb.nb - 1 : 0;
-    const u64 nw = (nc + 63) >> 6;
-    src += (u64)blockIdx.y * stride;
-    for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x) {
-        u64 v = src[w];
-        if (w == nw - 1 && (nc & 63)) v &= (~0ull) >> (64 - (nc & 63));
-        jb.c[w] = v;
-    }
-}
-
 inline unsigned blocks_for(u64 n, unsigned threads) { return (unsigned)((n + threads - 1) / threads); }
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
@@ -286,6 +162,11 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
                    u64 out_stride, cudaStream_t st)
 {
     if (l < 6) {
+        if (recording(ctx)) {
+            SegRec r{SEG_ENCODE_SMALL, {l, 0, 0, 0}, 1, (unsigned)count, 64, 0, 1, -1,
+                     {(u64)novel, nonzero_bits, (u64)ctx->d_enc, (u64)f, stride, out_stride}};
+            return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+        }
         k_encode_small<<<dim3(1, count), 64, 0, st>>>(novel, l, nonzero_bits, ctx->d_enc, f, stride, out_stride);
     } else {
         const u64 rw = 1ull << (l - 6), np = 1ull << l;
@@ -293,6 +174,11 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
         int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
         if (rows > 64) rows = 64;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        if (recording(ctx)) {
+            SegRec r{SEG_ENCODE, {rows, 0, 0, 0}, (unsigned)grid, (unsigned)count, 256, kCodecSmemWords * 8,
+                     (unsigned)grid, -1, {(u64)novel, rw, (u64)ctx->d_enc, (u64)f, groups, stride, out_stride}};
+            return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+        }
         launch_pdl(ctx->pdl, k_encode, dim3((unsigned)grid, count), dim3(256), 0, st, novel, rw, rows, ctx->d_enc, f, groups, stride,
                                                                out_stride);
     }
@@ -303,11 +189,21 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
 cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u64 stride, cudaStream_t st)
 {
     if (l < 6) {
+        if (recording(ctx)) {
+            SegRec r{SEG_DECODE_SMALL, {l, 0, 0, 0}, 1, (unsigned)count, 64, 64 * 8, 1, -1,
+                     {(u64)h, (u64)ctx->d_dec, (u64)novel, stride}};
+            return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+        }
         k_decode_small<<<dim3(1, count), 64, 0, st>>>(h, l, ctx->d_dec, novel, stride);
     } else {
         const u64 rw = 1ull << (l - 6);
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        if (recording(ctx)) {
+            SegRec r{SEG_DECODE, {0, 0, 0, 0}, (unsigned)grid, (unsigned)count, 256, kCodecSmemWords * 8,
+                     (unsigned)grid, -1, {(u64)h, rw, (u64)ctx->d_dec, (u64)novel, groups, stride}};
+            return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+        }
         launch_pdl(ctx->pdl, k_decode, dim3((unsigned)grid, count), dim3(256), 0, st, h, rw, ctx->d_dec, novel, groups, stride);
     }
     count_launch(ctx);
@@ -379,7 +275,13 @@ cudaError_t load_jobs(gf2x_ctx *ctx, const JobDev *jobs, int which, u64 *dst, u6
                       cudaStream_t st)
 {
     const u64 b = (dst_words + 255) / 256;
-    k_load_jobs<<<dim3((unsigned)(b < 1024 ? b : 1024), count), 256, 0, st>>>(jobs, which, dst, stride, dst_words);
+    const unsigned gx = (unsigned)(b < 1024 ? b : 1024);
+    if (recording(ctx)) {
+        SegRec r{SEG_LOAD_JOBS, {which, 0, 0, 0}, gx, (unsigned)count, 256, 0, gx, -1,
+                 {(u64)jobs, (u64)dst, stride, dst_words}};
+        return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    k_load_jobs<<<dim3(gx, count), 256, 0, st>>>(jobs, which, dst, stride, dst_words);
     count_launch(ctx);
     return cudaGetLastError();
 }
@@ -388,7 +290,12 @@ cudaError_t store_jobs(gf2x_ctx *ctx, const u64 *src, u64 stride, const JobDev *
                        cudaStream_t st)
 {
     const u64 b = (max_words + 255) / 256;
-    k_store_jobs<<<dim3((unsigned)(b < 1024 ? (b ? b : 1) : 1024), count), 256, 0, st>>>(src, stride, jobs);
+    const unsigned gx = (unsigned)(b < 1024 ? (b ? b : 1) : 1024);
+    if (recording(ctx)) {
+        SegRec r{SEG_STORE_JOBS, {0, 0, 0, 0}, gx, (unsigned)count, 256, 0, gx, -1, {(u64)src, stride, (u64)jobs}};
+        return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    k_store_jobs<<<dim3(gx, count), 256, 0, st>>>(src, stride, jobs);
     count_launch(ctx);
     return cudaGetLastError();
 }

@@ -12,7 +12,8 @@
 // is one launch on the caller's stream.
 //
 //   0 INT       32x32 integer multiplies on operands with 3-bit holes,
-//               Karatsuba over the 32-bit halves, two-step fold (gf64_mul)
+//               Karatsuba over the 32-bit halves, two-step fold (the earlier
+//               form of gf64_mul)
 //   1 INT_CONST the same with the constant's masked halves computed once
 //   2 TAB4      16 four-bit windows of a table in shared memory (mul_tab,
 //               the form the Butterfly kernels use)
@@ -20,7 +21,8 @@
 //   4 HYBRID    low 32 bits of x by 8 four-bit windows, high 32 bits by
 //               integer multiplies
 //   5 INT16     16x16 integer multiplies on operands with 2-bit holes (three
-//               residue classes, 32-bit products only), Karatsuba twice
+//               residue classes, 32-bit products only), Karatsuba twice: the
+//               form gf64_mul uses
 //   6 BITSLICE  64 elements of a warp as 64 bit-planes (lane t holds planes
 //               t and t + 32), the product by c as its 64x64 GF(2) matrix:
 //               every output plane XORs the input planes its row selects,
@@ -44,7 +46,16 @@ __device__ __forceinline__ u64 splitmix(u64 z)
     return z ^ (z >> 31);
 }
 
-// clmul32 with b given as its four masked classes.
+// The earlier integer form of gf64_mul (clmul32_h4: 32-bit operands, four classes).
+__device__ __forceinline__ u64 gf64_mul_h4(u64 a, u64 b)
+{
+    const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+    const u64 lo = clmul32_h4(al, bl), hi = clmul32_h4(ah, bh);
+    const u64 mid = clmul32_h4(al ^ ah, bl ^ bh) ^ lo ^ hi;
+    return gf64_reduce(hi ^ (mid >> 32), lo ^ (mid << 32));
+}
+
+// clmul32_h4 with b given as its four masked classes.
 __device__ __forceinline__ u64 clmul32_pre(u32 a, const u32 bm[4])
 {
     const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
@@ -63,38 +74,6 @@ __device__ __forceinline__ void mask4(u32 b, u32 bm[4])
     bm[1] = b & 0x22222222u;
     bm[2] = b & 0x44444444u;
     bm[3] = b & 0x88888888u;
-}
-
-// 16 x 16 -> 31-bit carry-less product: bits of one residue class mod 3 are
-// 3 apart; a class-by-class integer product has at most 6 terms per output
-// position, so the count fits in the 2-bit gap plus its own bit and its
-// parity is the carry-less bit.  Output positions of class k come from the
-// class pairs (i, j) with i + j = k mod 3.
-__device__ __forceinline__ u32 clmul16(u32 a, u32 b)
-{
-    const u32 m0 = 0x9249u, m1 = 0x2492u, m2 = 0x4924u;          // bits = 0, 1, 2 mod 3
-    const u32 a0 = a & m0, a1 = a & m1, a2 = a & m2;
-    const u32 b0 = b & m0, b1 = b & m1, b2 = b & m2;
-    const u32 z0 = (a0 * b0) ^ (a1 * b2) ^ (a2 * b1);
-    const u32 z1 = (a0 * b1) ^ (a1 * b0) ^ (a2 * b2);
-    const u32 z2 = (a0 * b2) ^ (a1 * b1) ^ (a2 * b0);
-    return (z0 & 0x49249249u) | (z1 & 0x12492492u) | (z2 & 0x24924924u);
-}
-
-__device__ __forceinline__ u64 clmul32_k16(u32 a, u32 b)
-{
-    const u32 al = a & 0xFFFFu, ah = a >> 16, bl = b & 0xFFFFu, bh = b >> 16;
-    const u32 lo = clmul16(al, bl), hi = clmul16(ah, bh);
-    const u32 mid = clmul16(al ^ ah, bl ^ bh) ^ lo ^ hi;
-    return (u64)lo ^ ((u64)mid << 16) ^ ((u64)hi << 32);
-}
-
-__device__ __forceinline__ u64 gf64_mul_k16(u64 a, u64 b)
-{
-    const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
-    const u64 lo = clmul32_k16(al, bl), hi = clmul32_k16(ah, bh);
-    const u64 mid = clmul32_k16(al ^ ah, bl ^ bh) ^ lo ^ hi;
-    return gf64_reduce(hi ^ (mid >> 32), lo ^ (mid << 32));
 }
 
 // Eight-bit windows: tab8[w * 256 + e] = c * (e x^(8w)).
@@ -118,7 +97,7 @@ __global__ void __launch_bounds__(kBenchThreads) k_field_bench(u64 seed, u64 c, 
     for (int k = 0; k < kChains; ++k) x[k] = splitmix(seed ^ (gid * kChains + k));
 
     if constexpr (V == FV_TAB4 || V == FV_HYBRID) {
-        build_tables(tab, 1, [&](int) { return c; });
+        build_tables(launch_block(), tab, 1, [&](int) { return c; });
     } else if constexpr (V == FV_TAB8) {
         for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) {
             const int w = k >> 8, e = k & 255;
@@ -137,7 +116,7 @@ __global__ void __launch_bounds__(kBenchThreads) k_field_bench(u64 seed, u64 c, 
     if constexpr (V == FV_INT) {
         for (int s = 0; s < steps; ++s)
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) x[k] = gf64_mul(c, x[k]);
+            for (int k = 0; k < kChains; ++k) x[k] = gf64_mul_h4(c, x[k]);
     } else if constexpr (V == FV_INT_CONST) {
         u32 cl[4], ch[4], cm[4];
         mask4((u32)c, cl);
@@ -181,7 +160,7 @@ __global__ void __launch_bounds__(kBenchThreads) k_field_bench(u64 seed, u64 c, 
     } else if constexpr (V == FV_INT16) {
         for (int s = 0; s < steps; ++s)
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) x[k] = gf64_mul_k16(c, x[k]);
+            for (int k = 0; k < kChains; ++k) x[k] = gf64_mul(c, x[k]);
     } else if constexpr (V == FV_BITSLICE) {
         // 64 elements per warp and vector: lane t holds elements t and t + 32
         // of two vectors (x[0], x[1]) and (x[2], x[3]); transposed, lane t

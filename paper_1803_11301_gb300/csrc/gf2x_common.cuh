@@ -2,9 +2,9 @@
 //
 // Field: GF(2^64) = GF(2)[x] / (x^64 + x^4 + x^3 + x + 1), polynomial form
 // (Sec. 4.3).  The GPU has no carry-less multiply instruction, so the product
-// is built from 32x32->64 integer multiplies on operands with "holes"
-// (every fourth bit kept, so no carry reaches a kept bit), Karatsuba over the
-// 32-bit halves, and a two-step fold of the high word by x^4 + x^3 + x + 1.
+// is built from 16x16-bit integer multiplies on operands with "holes" (every
+// third bit kept, so no carry reaches a kept bit), Karatsuba over the 16-bit
+// and 32-bit halves, and a two-step fold of the high word by x^4 + x^3 + x + 1.
 #pragma once
 
 #include <cstddef>
@@ -22,23 +22,60 @@ typedef uint32_t u32;
 #define GF2X_MOD_LOW 0x1Bull   // x^4 + x^3 + x + 1
 
 // ------------------------------------------------------------ field arithmetic
-// 32 x 32 -> 64-bit carry-less product by integer multiplication of operands
-// with "holes", the published constant-time technique of T. Pornin (BearSSL's
-// ghash_ctmul): a_i = a & (0x1111... << i) keeps one bit in four; the integer
-// product a_i * b_j has at most 8 terms per output position, so each count
-// fits in the 4-bit gap and its parity is the carry-less bit.  Positions of
-// class k (mod 4) come from the pairs i+j = k.
+// Carry-less products by integer multiplication of operands with "holes",
+// the published constant-time technique of T. Pornin (BearSSL's ghash_ctmul):
+// split each operand into residue classes of bit positions, so that the
+// integer product of two classes never carries into a kept bit, and keep in
+// each class of output positions the parity of its count.
+//
+// 16 x 16 -> 31 bits with three classes (bit positions mod 3): a class of a
+// 16-bit operand has at most 6 bits, so a class-by-class product has at most
+// 6 terms per output position, a count that fits in the position and the two
+// bits above it (the next position of the same class is 3 higher).  Output
+// positions of class k come from the class pairs (i, j) with i + j = k mod 3.
+// Nine 32-bit multiplies.  Measured on GB300 against 32-bit operands with four
+// classes (sixteen 32 x 32 -> 64-bit multiplies per 32-bit product): 155
+// against 129 Gmul/s for the GF(2^64) product (bench.py --stage field_mul).
+__device__ __forceinline__ u32 clmul16(u32 a, u32 b)
+{
+    const u32 m0 = 0x9249u, m1 = 0x2492u, m2 = 0x4924u;          // bits = 0, 1, 2 mod 3
+    const u32 a0 = a & m0, a1 = a & m1, a2 = a & m2;
+    const u32 b0 = b & m0, b1 = b & m1, b2 = b & m2;
+    const u32 z0 = (a0 * b0) ^ (a1 * b2) ^ (a2 * b1);
+    const u32 z1 = (a0 * b1) ^ (a1 * b0) ^ (a2 * b2);
+    const u32 z2 = (a0 * b2) ^ (a1 * b1) ^ (a2 * b0);
+    return (z0 & 0x49249249u) | (z1 & 0x12492492u) | (z2 & 0x24924924u);
+}
+
+// 32 x 32 -> 63 bits: Karatsuba over the 16-bit halves (GF2X_CLMUL32_H4 selects
+// the four-class form below at compile time, to measure one against the other).
+__device__ __forceinline__ u64 clmul32_h4(u32 a, u32 b);
 __device__ __forceinline__ u64 clmul32(u32 a, u32 b)
 {
+#ifdef GF2X_CLMUL32_H4
+    return clmul32_h4(a, b);
+#endif
+    const u32 al = a & 0xFFFFu, ah = a >> 16, bl = b & 0xFFFFu, bh = b >> 16;
+    const u32 lo = clmul16(al, bl), hi = clmul16(ah, bh);
+    const u32 mid = clmul16(al ^ ah, bl ^ bh) ^ lo ^ hi;
+    return (u64)lo ^ ((u64)mid << 16) ^ ((u64)hi << 32);
+}
+
+// 32 x 32 -> 63 bits with four classes (bit positions mod 4): at most 8 terms
+// per output position, a count that fits in 4 bits; sixteen 32 x 32 -> 64-bit
+// multiplies.  Slower than clmul32 but it needs fewer registers: the
+// GF(2^128) kernels (m128.cu), whose products hold twice the state, keep it.
+__device__ __forceinline__ u64 clmul32_h4(u32 a, u32 b)
+{
     const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
-    u32 a0 = a & m0, a1 = a & m1, a2 = a & m2, a3 = a & m3;
-    u32 b0 = b & m0, b1 = b & m1, b2 = b & m2, b3 = b & m3;
-    u64 z0 = ((u64)a0 * b0) ^ ((u64)a1 * b3) ^ ((u64)a2 * b2) ^ ((u64)a3 * b1);
-    u64 z1 = ((u64)a0 * b1) ^ ((u64)a1 * b0) ^ ((u64)a2 * b3) ^ ((u64)a3 * b2);
-    u64 z2 = ((u64)a0 * b2) ^ ((u64)a1 * b1) ^ ((u64)a2 * b0) ^ ((u64)a3 * b3);
-    u64 z3 = ((u64)a0 * b3) ^ ((u64)a1 * b2) ^ ((u64)a2 * b1) ^ ((u64)a3 * b0);
-    return (z0 & 0x1111111111111111ull) | (z1 & 0x2222222222222222ull) |
-           (z2 & 0x4444444444444444ull) | (z3 & 0x8888888888888888ull);
+    const u32 a0 = a & m0, a1 = a & m1, a2 = a & m2, a3 = a & m3;
+    const u32 b0 = b & m0, b1 = b & m1, b2 = b & m2, b3 = b & m3;
+    const u64 z0 = ((u64)a0 * b0) ^ ((u64)a1 * b3) ^ ((u64)a2 * b2) ^ ((u64)a3 * b1);
+    const u64 z1 = ((u64)a0 * b1) ^ ((u64)a1 * b0) ^ ((u64)a2 * b3) ^ ((u64)a3 * b2);
+    const u64 z2 = ((u64)a0 * b2) ^ ((u64)a1 * b1) ^ ((u64)a2 * b0) ^ ((u64)a3 * b3);
+    const u64 z3 = ((u64)a0 * b3) ^ ((u64)a1 * b2) ^ ((u64)a2 * b1) ^ ((u64)a3 * b0);
+    return (z0 & 0x1111111111111111ull) | (z1 & 0x2222222222222222ull) | (z2 & 0x4444444444444444ull) |
+           (z3 & 0x8888888888888888ull);
 }
 
 // (hi, lo) -> hi * x^64 + lo reduced: x^64 = x^4 + x^3 + x + 1.
@@ -99,6 +136,30 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
     }
 }
 
+// ------------------------------------------------------------ block bodies
+// The block a kernel body runs as: the launch's own block, or one sub-block of
+// the persistent batch kernel (persist.cu), which runs the blocks of many
+// launches in one grid.  Bodies take their block index, grid size, thread
+// index and thread count from here and synchronise their threads with sync().
+// A sub-block is a whole number of warps and has its own named barrier.
+struct VBlock {
+    unsigned bx, by;      // block index (y: the job of a batch)
+    unsigned gx, gy;      // grid size
+    unsigned t, nt;       // thread index and threads of the block
+    unsigned bar;         // 0: the whole CTA (__syncthreads); else a named barrier for nt threads
+    __device__ __forceinline__ void sync() const
+    {
+        if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    }
+};
+
+// The block of an ordinary launch.
+__device__ __forceinline__ VBlock launch_block()
+{
+    return VBlock{blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, threadIdx.x, blockDim.x, 0u};
+}
+
 // ------------------------------------------------ programmatic dependent launch
 // With `enable`, a kernel launched by launch_pdl may start while the kernel
 // before it in the stream is finishing.  Each of its blocks first lets its own
@@ -149,20 +210,79 @@ struct GridSync {
     unsigned pad;
 };
 
+// ------------------------------------------------------- recorded launches
+// gf2x_mul_batch can run all its size classes in one persistent launch
+// (persist.cu): the host code that would launch a class's kernels records each
+// launch instead (its block body, grid, block size, shared memory and
+// arguments), and the persistent kernel runs the recorded blocks from a device
+// work queue.  Bodies with the same thread count and arguments as the kernels.
+enum SegKind {
+    SEG_LOAD_JOBS = 0, SEG_STORE_JOBS, SEG_ENCODE, SEG_ENCODE_SMALL, SEG_DECODE, SEG_DECODE_SMALL, SEG_CVT_WIDE,
+    SEG_CVT_TILE, SEG_CVT_COL, SEG_CVT_TAYLOR, SEG_UNIT16, SEG_OUTER, SEG_TOP, SEG_BOTTOM, SEG_KIND_COUNT
+};
+
+struct SegRec {
+    int kind;                 // SegKind
+    int i[4];                 // small arguments (template choices, modes)
+    unsigned gx, gy;          // grid: gy is the job dimension of the class
+    unsigned threads;         // threads per block
+    unsigned smem;            // shared memory per block in bytes (static and dynamic)
+    unsigned per_job;         // blocks of one job: gx * (gy / jobs)
+    int blob;                 // byte offset of extra data in the recorder's blob (a BasisCvt plan), or -1
+    u64 a[10];                // pointers and sizes
+};
+
+struct Recorder {
+    SegRec *segs = nullptr;   // host arrays, grown by record()
+    int nseg = 0, cap = 0;
+    unsigned char *blob = nullptr;
+    size_t blob_bytes = 0, blob_cap = 0;
+    int jobs = 0;             // jobs of the class being recorded
+    bool unsupported = false; // a launch the persistent kernel cannot run
+    ~Recorder();
+};
+
+// The recorder of the class being planned, or null (launches run).
+inline Recorder *recording(const struct gf2x_ctx *ctx);
+// Append one launch; false (and the recorder marked unsupported) on failure.
+bool record(struct gf2x_ctx *ctx, const SegRec &r);
+// Append bytes to the blob (8-byte aligned); their offset, or -1.
+int record_blob(struct gf2x_ctx *ctx, const void *p, size_t n);
+// Persistent launches are limited to what one block of the persistent kernel
+// can hold: a segment needing more marks the recorder unsupported.
+// Device state of a context (one allocation): status word at 0, grid barrier
+// at 128, scratch word at 192, the queue of the wait self-test from 1024.
+constexpr size_t kStateBytes = 4096;
+constexpr size_t kStateQueueOffset = 1024;
+// A CTA of the persistent kernel: 256 threads; GF2X_PERSIST_BLOCKS CTAs per SM
+// (3: 80 registers a thread, 64 KiB of dynamic shared memory a CTA, bottom
+// tiles up to 2^10 points; 4: 64 registers, 46 KiB, tiles up to 2^9 points).
+#ifndef GF2X_PERSIST_BLOCKS
+#define GF2X_PERSIST_BLOCKS 3
+#endif
+constexpr unsigned kPersistThreads = 256;
+constexpr unsigned kPersistBlocksPerSM = GF2X_PERSIST_BLOCKS;
+constexpr unsigned kPersistSmem = kPersistBlocksPerSM >= 4 ? 46 * 1024 : 64 * 1024;
+constexpr int kPersistMaxDepth = kPersistBlocksPerSM >= 4 ? 9 : 10;
+constexpr unsigned kPersistMaxSegs = 384;            // recorded launches of one class
+constexpr size_t kPersistMaxPlanBytes = 64 * 1024;   // BasisCvt plans of one class
+
 // ------------------------------------------------------------------ context
 // Stages of Alg. 5 as the profiler and the launch counter see them.
 // STAGE_BOTTOM is the fused low-layer kernel of gf2x_mul: the bottom layers of
 // both forward Butterflies, the pointwise product and the bottom layers of the
 // iButterfly; STAGE_BUTTERFLY / STAGE_IBUTTERFLY then hold the top layers.
+// STAGE_PERSIST is the persistent batch kernel, every stage of every job.
 enum Gf2xStage {
     STAGE_LOAD = 0, STAGE_BASISCVT, STAGE_ENCODE, STAGE_BUTTERFLY, STAGE_POINTWISE,
-    STAGE_IBUTTERFLY, STAGE_DECODE, STAGE_IBASISCVT, STAGE_STORE, STAGE_BOTTOM, STAGE_COUNT
+    STAGE_IBUTTERFLY, STAGE_DECODE, STAGE_IBASISCVT, STAGE_STORE, STAGE_BOTTOM, STAGE_PERSIST, STAGE_COUNT
 };
 
 struct gf2x_ctx {
     int device;
     int num_sms;
     u64 *d_tables;      // one allocation holding the tables below
+    void *d_state;      // kStateBytes of device state: status word, barrier, scratch word, self-test queue
     u64 *d_cvt;         // 8 x 256: Cantor coordinates -> polynomial form
     u64 *d_enc;         // 8 x 256: bits (a_{j n_p + i})_j -> f_i  (matrix R)
     u64 *d_dec;         // 8 x 256: f_i -> bits                    (matrix R^{-1})
@@ -187,7 +307,10 @@ struct gf2x_ctx {
     void *batch_graphs;                 // CUDA graph cache of gf2x_mul_batch
     void *tuner;                        // measured launch-shape choices, see tune.cu
     bool pdl;                           // launch_pdl overlaps kernels (set per product by size)
+    Recorder *rec;                      // set while gf2x_mul_batch records a class (persist.cu)
 };
+
+inline Recorder *recording(const gf2x_ctx *ctx) { return ctx->rec; }
 
 // Count one kernel launch against the current stage.
 inline void count_launch(gf2x_ctx *ctx, int n = 1) { ctx->launches[ctx->stage] += (unsigned long long)n; }
@@ -200,7 +323,7 @@ namespace gf2x {
 // The same numbers as the GF2X_KNOB_* constants of the C ABI.
 enum TuneKnob {
     TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3, TUNE_M128_BOTTOM_CHUNK = 4, TUNE_BFLY_DEPTH = 5,
-    TUNE_M128_BFLY_DEPTH = 6, TUNE_KNOB_END = 7
+    TUNE_M128_BFLY_DEPTH = 6, TUNE_BATCH_PERSIST = 7, TUNE_KNOB_END = 8
 };
 void *tuner_create();
 void tuner_destroy(void *t);
@@ -302,5 +425,30 @@ cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u6
 // never through the CUDA graph cache (api.cu).
 gf2x_status mul_uncached(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64 nb, u64 *c, void *ws,
                          size_t ws_bytes, cudaStream_t st);
+
+// ---- the persistent batch launch (persist.cu)
+// Device bytes it needs for `classes` size classes and `jobs` jobs in all: a
+// bound that depends on those counts only.
+size_t persist_area_bytes(size_t classes, size_t jobs);
+// Whether the persistent kernel can run every launch a recorder holds.
+bool persist_supported(const Recorder &r);
+// The recorded classes, laid out in the device area (256-byte aligned, at
+// least persist_area_bytes) by persist_prepare, which uploads them on `st`.
+struct PersistLaunch {
+    void *segs, *done, *state;
+    int nseg;
+    unsigned items, grid;
+    size_t done_bytes;
+    u64 digest;           // of the uploaded plan: launches with equal digests run the same work
+};
+cudaError_t persist_prepare(gf2x_ctx *ctx, const Recorder *const *recs, int classes, void *area, size_t area_bytes,
+                            cudaStream_t st, PersistLaunch *out);
+// Clears the queue state and launches the persistent kernel (capturable).
+// limit_ns bounds every wait (0: the default of 2 s).
+cudaError_t persist_launch(gf2x_ctx *ctx, const PersistLaunch &pl, cudaStream_t st, unsigned long long limit_ns = 0);
+// Self-test of the queue's bounded waits: a two-item queue whose second item
+// waits on a first that can never finish; the wait runs out after limit_ns and
+// records GF2X_ETIMEOUT.  Uses the context's own state area.
+cudaError_t persist_selftest_timeout(gf2x_ctx *ctx, cudaStream_t st, unsigned long long limit_ns);
 
 }  // namespace gf2x

@@ -60,11 +60,11 @@ __device__ __forceinline__ u64 mul_x(u64 p) { return (p << 1) ^ ((p >> 63) * GF2
 
 // Build nt tables: thread (t, w) computes the powers c x^(4w+b), b < 4, of
 // twiddle c = twid(t) and writes the 16 entries of window w (Gray-code XORs).
-// Ends with __syncthreads().
+// Ends with the block's barrier.
 template <class F>
-__device__ __forceinline__ void build_tables(u64 *tabs, int nt, F twid)
+__device__ __forceinline__ void build_tables(const VBlock &vb, u64 *tabs, int nt, F twid)
 {
-    for (int k = threadIdx.x; k < nt * 16; k += blockDim.x) {
+    for (int k = vb.t; k < nt * 16; k += vb.nt) {
         const int t = k >> 4, w = k & 15;
         const u64 c = twid(t);
         u64 p[4];
@@ -81,7 +81,7 @@ __device__ __forceinline__ void build_tables(u64 *tabs, int nt, F twid)
             dst[(g ^ (g >> 1)) ^ w] = e;
         }
     }
-    __syncthreads();
+    vb.sync();
 }
 
 }  // namespace gf2x

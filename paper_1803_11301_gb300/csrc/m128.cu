@@ -14,7 +14,7 @@
 // words and its 16 high words in two 128-byte rows, so one lookup is two
 // 8-byte loads that never conflict across the 32 lanes.  Other products
 // (low layers, pointwise) use the integer form: Karatsuba over three 64 x 64
-// carry-less products, each three 32 x 32 ones (clmul32), and a fold of the
+// carry-less products, each three 32 x 32 ones (clmul32_h4), and a fold of the
 // high half by x^7 + x^2 + x + 1.
 #include <algorithm>
 #include <vector>
@@ -70,8 +70,8 @@ __device__ __forceinline__ void st128(u64 *p, g128 v) { *(ulonglong2 *)p = make_
 __device__ __forceinline__ void clmul64(u64 a, u64 b, u64 &lo, u64 &hi)
 {
     const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
-    const u64 l = clmul32(al, bl), h = clmul32(ah, bh);
-    const u64 m = clmul32(al ^ ah, bl ^ bh) ^ l ^ h;
+    const u64 l = clmul32_h4(al, bl), h = clmul32_h4(ah, bh);
+    const u64 m = clmul32_h4(al ^ ah, bl ^ bh) ^ l ^ h;
     lo = l ^ (m << 32);
     hi = h ^ (m >> 32);
 }

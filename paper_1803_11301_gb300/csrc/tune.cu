@@ -95,7 +95,7 @@ int tune_choice(gf2x_ctx *ctx, int knob, u64 key, const int *cands, int ncand, i
     for (const TuneEntry &e : c->entries)
         if (e.knob == knob && e.key == key) return e.choice;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (c->disabled || c->frozen || ncand < 2 || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+    if (c->disabled || c->frozen || ncand < 2 || recording(ctx) || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
         cs != cudaStreamCaptureStatusNone)
         return fallback;
     cudaEvent_t e0, e1;

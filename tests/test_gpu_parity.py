@@ -336,6 +336,50 @@ def test_batch_uneven_lengths_bit_exact(ctx):
             assert np.array_equal(host_words(c, nc), O.mul(a, na, b, nb)), (rep, na, nb)
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_batch_persistent_and_class_launches(ctx, persistent):
+    # the batch as one persistent launch (device work queue) and as one launch
+    # per kernel and size class: both bit-exact against the oracle, on call 1
+    # (direct), 2 (captured) and 3 (replayed)
+    from paper_1803_11301_gb300 import KNOB_BATCH_PERSISTENT
+    lens = synth.loguniform_lengths(synth.config_seed(4, 8), 240, 6.0, 19.0).reshape(120, 2)
+    lengths = [(int(x), int(y)) for x, y in lens] + [(1, 1), (64, 64), (1 << 18, 3), (0, 9), (1 << 19, 1 << 19)]
+    jobs, hostops = _batch_jobs(ctx, lengths, 45)
+    ctx.tune_pin(KNOB_BATCH_PERSISTENT, persistent)
+    try:
+        for rep in range(3):
+            for j in jobs:
+                j[4].fill_(-1)
+            ctx.profile_enable(False)
+            ctx.mul_batch(jobs)
+            launches = ctx.profile_read()
+            for (da, na, db, nb, c), (a, b) in zip(jobs, hostops):
+                nc = na + nb - 1 if na and nb else 0
+                if nc:
+                    assert np.array_equal(host_words(c, nc), O.mul(a, na, b, nb)), (persistent, rep, na, nb)
+            if persistent:
+                assert launches["persistent_batch"][1] == 1, launches      # the whole batch: one launch
+                assert sum(v[1] for v in launches.values()) == 1
+            else:
+                assert launches["persistent_batch"][1] == 0
+        assert ctx.stream_status() == 0
+    finally:
+        ctx.tune_pin(KNOB_BATCH_PERSISTENT, -1)
+
+
+def test_batch_queue_wait_times_out(ctx):
+    # a queue item whose dependency can never finish: its bounded wait runs
+    # out, GF2X_ETIMEOUT is recorded, the kernel returns and the context works
+    ctx.selftest_queue_timeout()
+    assert ctx.stream_status() == 5
+    assert ctx.stream_status() == 0
+    lens = [(1000, 3000), (1 << 16, 1 << 15)]
+    jobs, hostops = _batch_jobs(ctx, lens, 46)
+    ctx.mul_batch(jobs)
+    for (da, na, db, nb, c), (a, b) in zip(jobs, hostops):
+        assert np.array_equal(host_words(c, na + nb - 1), O.mul(a, na, b, nb))
+
+
 def host_words(t, nbits):
     return host(t)[: (nbits + 63) // 64]
 
@@ -377,6 +421,103 @@ def test_serving_results_same_alone_and_in_the_mix(ctx):
         assert torch.equal(got, alone), r.tag                              # alone and in the mix
         want = O.mul(pool_h[r.tag % 4], r.na, pool_h[(r.tag + 1) % 4], r.nb)
         assert np.array_equal(host(got), want), r.tag                      # and the oracle's product
+
+
+def test_serving_rejects_a_request_beyond_the_budget(ctx):
+    # a request that could not run even alone within the budget is refused at
+    # admission with GF2X_ENOMEM and never queued; the others are served
+    import torch
+    from paper_1803_11301_gb300.serving import GF2X_ENOMEM, GF2X_OK, Request, Server
+    srv = Server(ctx, streams=2, memory_budget=64 << 20)
+    small = dev(synth.operand(synth.config_seed(5, 401), 1 << 14))
+    big = dev(synth.operand(synth.config_seed(5, 402), 1 << 26))
+    ok1 = Request(small, 1 << 14, small, 5000, tag=1)
+    huge = Request(big, 1 << 26, big, 1 << 26, tag=2)          # 3 x 16 MiB of workspace and more
+    ok2 = Request(small, 3000, small, 1 << 14, tag=3)
+    assert srv.submit(ok1) == GF2X_OK
+    assert srv.submit(huge) == GF2X_ENOMEM
+    assert srv.submit(ok2) == GF2X_OK
+    assert huge.state == "rejected" and huge not in srv.pending and srv.rejected == [huge]
+    srv.drain()
+    torch.cuda.synchronize()
+    sh = host(small)
+    for r in (ok1, ok2):
+        assert r.state == "done"
+        assert np.array_equal(host_words(r.out, r.na + r.nb - 1), O.mul(sh, r.na, sh, r.nb))
+
+
+def test_serving_cancels_pending_requests(ctx):
+    # requests cancelled before a batch takes them never run; the rest are exact
+    import torch
+    from paper_1803_11301_gb300.serving import Request, Server
+    srv = Server(ctx, streams=1, max_batch=4)
+    pool = dev(synth.operand(synth.config_seed(5, 410), 1 << 16))
+    ph = host(pool)
+    reqs = [Request(pool, 1000 + 37 * k, pool, 2000 + 11 * k, tag=k) for k in range(24)]
+    for r in reqs:
+        srv.submit(r)
+    srv.poll()                                       # one batch of 4 takes the first requests
+    assert srv.cancel(reqs[0]) is False             # already running
+    gone = [reqs[k] for k in (5, 9, 17, 23)]
+    for r in gone:
+        assert srv.cancel(r) is True
+        assert srv.cancel(r) is False               # only once
+    srv.drain()
+    torch.cuda.synchronize()
+    for r in reqs:
+        if r in gone:
+            assert r.state == "cancelled" and r.batch_id == -1
+        else:
+            assert r.state == "done"
+            assert np.array_equal(host_words(r.out, r.na + r.nb - 1), O.mul(ph, r.na, ph, r.nb)), r.tag
+
+
+def test_serving_resident_transform_of_a_recurring_operand(ctx):
+    # the same b (named by b_key) recurs: from its second use on, its transform
+    # stays on the device and the products skip b's forward steps; every
+    # result equals the oracle's
+    import torch
+    from paper_1803_11301_gb300.serving import Request, Server
+    srv = Server(ctx, streams=3, max_batch=8, reuse_after=2)
+    b = dev(synth.operand(synth.config_seed(5, 420), 20000))
+    pool = [dev(synth.operand(synth.config_seed(5, 421 + k), 30000)) for k in range(3)]
+    bh, poolh = host(b), [host(t) for t in pool]
+    reqs = []
+    for k in range(40):
+        r = Request(pool[k % 3], 30000 - 97 * (k % 5), b, 20000, tag=k, b_key="b20000")
+        reqs.append(r)
+        srv.submit(r)
+        if k % 3 == 0:
+            srv.poll()
+    srv.drain()
+    torch.cuda.synchronize()
+    assert sum(r.reused for r in reqs) >= 30
+    for r in reqs:
+        want = O.mul(poolh[r.tag % 3], r.na, bh, r.nb)
+        assert np.array_equal(host_words(r.out, r.na + r.nb - 1), want), r.tag
+
+
+def test_serving_host_operands(ctx):
+    # page-locked host operands: copied in and out on the batch's stream
+    import torch
+    from paper_1803_11301_gb300.serving import Request, Server
+    srv = Server(ctx, streams=2, max_batch=8)
+    words = [synth.operand(synth.config_seed(5, 430 + k), 1 << 17) for k in range(2)]
+    pinned = [torch.from_numpy(w.view(np.int64)).pin_memory() for w in words]
+    lens = synth.loguniform_lengths(synth.config_seed(5, 431), 60, 8.0, 17.0).reshape(30, 2)
+    reqs = []
+    for k, (na, nb) in enumerate(lens):
+        na, nb = int(na), int(nb)
+        r = Request(pinned[0][: (na + 63) // 64], na, pinned[1][: (nb + 63) // 64], nb, tag=k, host=True)
+        reqs.append(r)
+        srv.submit(r)
+        srv.poll()
+    srv.drain()
+    torch.cuda.synchronize()
+    for r in reqs:
+        assert r.out.device.type == "cpu" and r.out.is_pinned()
+        got = r.out.numpy().view(np.uint64)[: (r.na + r.nb - 1 + 63) // 64]
+        assert np.array_equal(got, O.mul(words[0], r.na, words[1], r.nb)), r.tag
 
 
 # ------------------------------------------------------------ reused operand
