@@ -648,8 +648,9 @@ def run_batch(args, world, rank, local):
     from paper_1803_11301_gb300 import KNOB_BATCH_PERSISTENT
 
     def timed_batch(mode):
-        """K batch calls, one persistent launch each (mode 1) or one launch per kernel and size class (0)."""
-        ctx.tune_pin(KNOB_BATCH_PERSISTENT, mode)
+        """K batch calls: one persistent launch each (mode 1), one launch per kernel and size class (0),
+        or the library's choice (None: the tuner times both on the first call)."""
+        ctx.tune_pin(KNOB_BATCH_PERSISTENT, -1 if mode is None else mode)
         ctx.profile_enable(True)
         for _ in range(args.warmup):
             flush.fill_(1)
@@ -677,10 +678,13 @@ def run_batch(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
     class_ms, class_prof = timed_batch(0)
-    total_ms, prof = timed_batch(1)
+    pers_ms, pers_prof = timed_batch(1)
+    total_ms, prof = timed_batch(None)
     clk = clocks.stop()
     value = world * count * args.steps / (total_ms / 1e3)
     class_value = world * count * args.steps / (class_ms / 1e3)
+    pers_value = world * count * args.steps / (pers_ms / 1e3)
+    chose = "persistent" if prof.get("persistent_batch", (0, 0))[1] else "class launches"
     # one gf2x_mul per product (sequential calls on the same stream), one pass after one warm-up pass
     wsp = torch.empty(max(workspace_bytes(j[1], j[3]) for j in jobs), dtype=torch.uint8, device=dev)
     for j in jobs:
@@ -746,8 +750,12 @@ def run_batch(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": CONFIGS[4]["name"], "products": count,
                        "l2": "flushed before every timed step (256 MiB write)"},
-            "batch_mode": "one persistent launch per batch (device work queue)",
+            "batch_mode": f"the library's choice, timed on the first call: {chose}",
+            "persistent": {"value": pers_value, "unit": "products/s", "ms_per_step": pers_ms / args.steps,
+                           "gpu_launches": int(sum(v[1] for v in pers_prof.values()) / args.steps),
+                           "how": "one persistent launch per batch (device work queue), graph replay"},
             "class_launches": {"value": class_value, "unit": "products/s", "ms_per_step": class_ms / args.steps,
+                               "stages_ms": {k: round(v[0] / args.steps, 4) for k, v in class_prof.items()},
                                "gpu_launches": int(sum(v[1] for v in class_prof.values()) / args.steps),
                                "how": "the same call with one launch per kernel and size class, graph replay"},
             "plain": {"value": plain, "unit": "products/s", "how": "one gf2x_mul call per product, same stream"},
@@ -935,6 +943,12 @@ def run_serving(args, world, rank, local):
 
     loads = {str(x): served_at(x) for x in (0.5, 0.8, 1.0)}
     headline = loads["0.8"]
+    from paper_1803_11301_gb300 import KNOB_BATCH_PERSISTENT
+    modes = {}
+    for name, m in (("persistent", 1), ("class_launches", 0)):     # the server's batches pinned to one way
+        ctx.tune_pin(KNOB_BATCH_PERSISTENT, m)
+        modes[name] = served_at(0.8)
+    ctx.tune_pin(KNOB_BATCH_PERSISTENT, -1)
     # one gf2x_mul per request, in arrival order on one stream, at 0.8 x saturated
     stream = torch.cuda.current_stream(dev)
     wsp = torch.empty(max(workspace_bytes(na, nb) for na, nb in sizes), dtype=torch.uint8, device=dev)
@@ -957,8 +971,30 @@ def run_serving(args, world, rank, local):
             plain_lat.append(1e3 * (now - t))
     pwall = replay(np.cumsum(gaps01 / (0.8 * sat)), p_submit, p_poll, lambda: not plain_pending)
     plain = {"products_per_s": count / pwall, "p50_ms": percentile(plain_lat, 50), "p99_ms": percentile(plain_lat, 99)}
-    # end to end: page-locked host operands, copies to and from the device inside the latency
-    e2e_run = served_at(0.8, host=True)
+    # end to end: page-locked host operands, copies to and from the device inside the latency,
+    # at 0.8 x its own saturated rate
+    s3 = server()
+    t0 = time.perf_counter()
+    for k in range(count):
+        s3.submit(make(k, host=True))
+    s3.drain()
+    sat_e2e = count / (time.perf_counter() - t0)
+
+    def served_host(load):
+        arrivals = np.cumsum(gaps01 / (load * sat_e2e))
+        s4 = server()
+        reqs = []
+
+        def s_submit(k, t):
+            r = make(k, True)
+            r.arrival = t
+            reqs.append(r)
+            s4.submit(r)
+        wall = replay(arrivals, s_submit, s4.poll, lambda: not s4.pending and not s4.inflight)
+        lat = [1e3 * (r.done - r.arrival) for r in reqs if r.state == "done"]
+        return {"load": load, "products_per_s": count / wall, "p50_ms": percentile(lat, 50),
+                "p99_ms": percentile(lat, 99), "saturated_products_per_s": sat_e2e}
+    e2e_run = served_host(0.8)
     clk = clocks.stop()
     h2d = sum(8 * ((na + 63) // 64 + (nb + 63) // 64) for na, nb in sizes) / count
     d2h = sum(8 * ((na + nb - 1 + 63) // 64) for na, nb in sizes) / count
@@ -968,9 +1004,10 @@ def run_serving(args, world, rank, local):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": CONFIGS[5]["name"], "requests": count, "load": 0.8,
                        "saturated_products_per_s": sat, "reuse_frac": args.reuse_frac},
-            "served": headline, "loads": loads, "plain_one_call_per_request": plain,
+            "served": headline, "loads": loads, "batch_modes_at_0.8": modes, "plain_one_call_per_request": plain,
             "e2e": {"value": e2e_run["products_per_s"], "unit": "products/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "p50_ms": e2e_run["p50_ms"], "p99_ms": e2e_run["p99_ms"],
+                    "load": 0.8, "saturated_products_per_s": sat_e2e,
                     "how": "page-locked host operands; the server copies them in and the product out on the "
                            "batch's stream, inside each request's latency; bytes per request"},
             "clocks": clk}

@@ -54,7 +54,8 @@ typedef enum {
     GF2X_ECUDA = 4,      /* a CUDA call or launch failed */
     GF2X_ETIMEOUT = 5,   /* a bounded device-side wait expired */
     GF2X_ENODEV = 6,     /* no usable CUDA device */
-    GF2X_ENOSPACE = 7    /* workspace smaller than gf2x_workspace_bytes() */
+    GF2X_ENOSPACE = 7,   /* workspace smaller than gf2x_workspace_bytes() */
+    GF2X_EBOUNDS = 8     /* a kernel met an index out of range (builds with GF2X_DEBUG_BOUNDS only) */
 } gf2x_status;
 
 typedef struct gf2x_ctx gf2x_ctx;
@@ -193,19 +194,24 @@ typedef struct gf2x_job {
 GF2X_API size_t gf2x_batch_workspace_bytes(const gf2x_job *jobs, size_t count);
 
 /* Many independent products of uneven lengths in one call (Alg. 5 for each).
- * The jobs are grouped by transform length n (size classes).  By default the
- * whole batch is ONE persistent kernel launch: the host plans every class's
- * stages (load, BasisCvt, Encode, Butterfly with the pointwise product,
- * Decode, iBasisCvt, store) as a device work queue, which a grid of one or
- * two blocks per SM drains; a job's next stage starts as soon as that job's
- * previous stage is done, and classes run side by side.  Every wait in the
- * queue is bounded: if one runs out (it cannot in a correct plan) the launch
- * records GF2X_ETIMEOUT in the context status word (gf2x_stream_status) and
- * returns without finishing the batch.  Batches whose stages need a launch
- * shape the persistent kernel lacks (transforms above 2^25 bits), or with
- * GF2X_KNOB_BATCH_PERSISTENT pinned to 0, run one launch per kernel and class
- * instead (the kernels' second grid dimension is the job).  Either way the
- * results are the same.  The host array `jobs` is read during the call and
+ * The jobs are grouped by transform length n (size classes).  Two ways to
+ * run them, with the same results:
+ *   - one launch per kernel and class (the kernels' second grid dimension is
+ *     the job);
+ *   - ONE persistent kernel launch for the whole batch: the host plans every
+ *     class's stages (load, BasisCvt, Encode, Butterfly with the pointwise
+ *     product, Decode, iBasisCvt, store) as a device work queue, which a grid
+ *     of three blocks per SM drains; a job's next stage starts as soon as that
+ *     job's previous stage is done, and classes run side by side.  Every wait
+ *     in the queue is bounded: if one runs out (it cannot in a correct plan)
+ *     the launch records GF2X_ETIMEOUT in the context status word
+ *     (gf2x_stream_status) and returns without finishing the batch.
+ * GF2X_KNOB_BATCH_PERSISTENT pins the choice; otherwise the first batch of
+ * each shape (job and class counts in power-of-two buckets) times both and the
+ * faster is kept (the class launches unless the persistent launch is more than
+ * 3% faster), like the other launch shapes.  Batches with transforms above
+ * 2^25 bits always run class launches (the persistent kernel lacks their
+ * launch shapes).  The host array `jobs` is read during the call and
  * copied to the workspace, with the queue; every device buffer follows the
  * gf2x_mul rules (8-byte aligned, c disjoint from a, b and the workspace;
  * jobs may share operands but not results).  Jobs with na or nb = 0 write
@@ -232,7 +238,10 @@ GF2X_API gf2x_status gf2x_selftest_queue_timeout(gf2x_ctx *ctx, void *stream);
 /* Read, and reset to GF2X_OK, the context's device status word after the
  * work already enqueued on `stream` has finished (synchronises the stream).
  * Device code records bounded-wait expiry (GF2X_ETIMEOUT) there; it never
- * traps. */
+ * traps.  A library built with GF2X_DEBUG_BOUNDS also range-checks the
+ * kernels' main global indices (an index out of range is counted and its
+ * access skipped); this call then returns GF2X_EBOUNDS if any was met since
+ * the last call, and resets the counts. */
 GF2X_API gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream);
 
 /* Launch shapes (bottom-tile depth, block shapes, table chunks, BasisCvt
@@ -256,8 +265,8 @@ GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
  *   GF2X_KNOB_M128_BOTTOM_CHUNK  GF(2^128) bottom kernel tables per chunk: 4, 8
  *   GF2X_KNOB_BOTTOM_DEPTH       Butterfly layers in the bottom kernel: 8 .. 11
  *   GF2X_KNOB_M128_BOTTOM_DEPTH  the same for GF(2^128) points: 8 .. 10
- *   GF2X_KNOB_BATCH_PERSISTENT   gf2x_mul_batch: 1 (one persistent launch, the
- *                                default) or 0 (one launch per kernel and size class)
+ *   GF2X_KNOB_BATCH_PERSISTENT   gf2x_mul_batch: 1 (one persistent launch) or 0 (one
+ *                                launch per kernel and size class)
  * GF2X_EINVAL for a NULL context, an unknown knob or choice < -1.  Not
  * thread-safe against calls running on the same context. */
 enum {

@@ -16,7 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-from .build import LIB as LIB_PATH
+from .build import LIB as LIB_PATH, LIB_DEBUG as LIB_DEBUG_PATH
 
 __all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_bits", "workspace_bytes",
            "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
@@ -24,7 +24,7 @@ __all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_b
            "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH", "KNOB_BATCH_PERSISTENT"]
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
-          5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE"}
+          5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE", 8: "GF2X_EBOUNDS"}
 
 _P = ctypes.c_void_p
 _U64 = ctypes.c_uint64
@@ -116,13 +116,15 @@ class Gf2xError(RuntimeError):
 
 
 def load_library() -> ctypes.CDLL:
-    """Load libgf2x_gb300.so (built by ``paper_1803_11301_gb300.build``); raise if absent."""
+    """Load libgf2x_gb300.so (built by ``paper_1803_11301_gb300.build``); raise if absent.
+    With GF2X_DEBUG_BOUNDS=1 in the environment, the range-checking build instead."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1803_11301_gb300.build` "
+        path = LIB_DEBUG_PATH if os.environ.get("GF2X_DEBUG_BOUNDS") == "1" else LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run `python -m paper_1803_11301_gb300.build` "
                               "(there is no CPU fallback)")
-        lib = ctypes.CDLL(LIB_PATH)
+        lib = ctypes.CDLL(path)
         for name, (res, args) in ABI_FUNCTIONS.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -174,6 +176,7 @@ class Context:
         _check(self._lib.gf2x_ctx_create(ctypes.byref(h), device), "gf2x_ctx_create")
         self._h = h
         self._ws = None
+        self._allocator = None
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -211,13 +214,26 @@ class Context:
         import torch
         return torch.empty(max(count, 1), dtype=torch.int64, device=self._dev())[:count]
 
+    def set_allocator(self, allocator=None):
+        """Workspaces the calls allocate come from allocator(nbytes) -> a CUDA uint8 tensor, or
+        None when it cannot (the call then raises GF2X_ENOMEM and enqueues nothing); None
+        restores torch's allocator."""
+        self._allocator = allocator
+        self._ws = None
+
     def workspace(self, nbytes: int):
         """A cached device workspace of at least nbytes (256-byte aligned)."""
         import torch
         if self._ws is None or self._ws.numel() < nbytes:
-            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self._dev())
-            if self._ws.data_ptr() % 256:
+            if self._allocator is not None:
+                ws = self._allocator(max(nbytes, 256))
+                if ws is None:
+                    raise Gf2xError(3, "workspace allocation")
+            else:
+                ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self._dev())
+            if ws.data_ptr() % 256:
                 raise RuntimeError("workspace allocation is not 256-byte aligned")
+            self._ws = ws
         return self._ws
 
     # --------------------------------------------------------- the product

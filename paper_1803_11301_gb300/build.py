@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB_NAME = "libgf2x_gb300.so"
 LIB = os.path.join(OUT, LIB_NAME)
+# The same library built with GF2X_DEBUG_BOUNDS (the kernels range-check their
+# main global indices and count what falls outside, see include/gf2x.h).
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, LIB_NAME)
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,25 +43,28 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile every CUDA source and link the shared library; return its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug_bounds: bool = False) -> str:
+    """Compile every CUDA source and link the shared library; return its path.
+    debug_bounds: the GF2X_DEBUG_BOUNDS library, in its own directory."""
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug_bounds else (OUT, LIB)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DGF2X_DEBUG_BOUNDS"] if debug_bounds else [])
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [cc, *ARCH, *flags, *PER_FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
@@ -73,11 +80,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -770,6 +770,7 @@ const char *gf2x_status_string(gf2x_status s)
     case GF2X_ETIMEOUT: return "GF2X_ETIMEOUT";
     case GF2X_ENODEV: return "GF2X_ENODEV";
     case GF2X_ENOSPACE: return "GF2X_ENOSPACE";
+    case GF2X_EBOUNDS: return "GF2X_EBOUNDS";
     }
     return "GF2X_UNKNOWN";
 }
@@ -1099,6 +1100,10 @@ gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream)
         TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
         TRY(cudaStreamSynchronize(st));
     }
+    const unsigned long long oob = gf2x::out_of_range_fft() + gf2x::out_of_range_cvt() +
+                                   gf2x::out_of_range_cvt_reg() + gf2x::out_of_range_bfly() +
+                                   gf2x::out_of_range_persist();
+    if (h == 0 && oob) return GF2X_EBOUNDS;
     return (gf2x_status)h;
 }
 
@@ -1302,44 +1307,66 @@ gf2x_status gf2x_mul_batch(gf2x_ctx *ctx, const gf2x_job *jobs, size_t count, vo
     // the job table goes to the device before the kernels (every call)
     TRY(cudaMemcpyAsync(ws, bp.table.data(), bp.table.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st));
     const std::vector<ClassRun> runs = bind_runs(bp, ws);
-    // One persistent launch (persist.cu) unless the knob asks for class launches or a class
-    // needs a launch shape the persistent kernel does not have: record every class's
-    // launches, upload the plan, and the launch itself is what runs (and is captured).
-    static const int modes[2] = {0, 1};
-    bool persistent = gf2x::tune_pinned(ctx, gf2x::TUNE_BATCH_PERSIST, modes, 2, 1) == 1;
+    // Two ways to run the classes, same results: one launch per kernel and class, or one
+    // persistent launch for the whole batch (persist.cu: every class's launches recorded,
+    // the plan uploaded to the workspace, one kernel drains it).  A pinned knob decides;
+    // else the tuner times both on the first batch of each shape (job and class counts in
+    // power-of-two buckets) and keeps the faster, the class launches unless the persistent
+    // launch is more than 3% faster; a batch with a launch shape the persistent kernel lacks
+    // runs class launches.
     gf2x::PersistLaunch pl{};
     u64 plan_digest = 0;
-    if (persistent) {
+    auto prepare_persistent = [&](cudaStream_t s2) -> gf2x_status {
         std::vector<Recorder> recs(runs.size());
         std::vector<const Recorder *> rp;
-        for (size_t c = 0; c < runs.size() && persistent; ++c) {
+        for (size_t c = 0; c < runs.size(); ++c) {
             recs[c].jobs = runs[c].count;
             ctx->rec = &recs[c];
-            const gf2x_status rs = run_class(ctx, runs[c], st);
+            const gf2x_status rs = run_class(ctx, runs[c], s2);
             ctx->rec = nullptr;
-            persistent = rs == GF2X_OK && gf2x::persist_supported(recs[c]);
+            if (rs != GF2X_OK || !gf2x::persist_supported(recs[c])) return GF2X_EINVAL;
             rp.push_back(&recs[c]);
         }
-        if (persistent) {
-            const int saved = ctx->stage;
-            ctx->stage = STAGE_PERSIST;
-            const cudaError_t pe = gf2x::persist_prepare(ctx, rp.data(), (int)rp.size(), (char *)ws + bp.persist_off,
-                                                         bp.persist_bytes, st, &pl);
-            ctx->stage = saved;
-            if (pe != cudaSuccess) return GF2X_ECUDA;
-            plan_digest = pl.digest;
-        }
-    }
-    auto run_all = [&](cudaStream_t s2) -> gf2x_status {
-        if (persistent) {
-            StageScope sc(ctx, STAGE_PERSIST, s2);
-            return from_cuda(gf2x::persist_launch(ctx, pl, s2));
-        }
+        const int saved = ctx->stage;
+        ctx->stage = STAGE_PERSIST;
+        const cudaError_t pe = gf2x::persist_prepare(ctx, rp.data(), (int)rp.size(), (char *)ws + bp.persist_off,
+                                                     bp.persist_bytes, s2, &pl);
+        ctx->stage = saved;
+        if (pe != cudaSuccess) return GF2X_ECUDA;
+        plan_digest = pl.digest;
+        return GF2X_OK;
+    };
+    auto run_classes = [&](cudaStream_t s2) -> gf2x_status {
         for (const ClassRun &r : runs) {
             gf2x_status e = run_class(ctx, r, s2);
             if (e != GF2X_OK) return e;
         }
         return GF2X_OK;
+    };
+    static const int modes[2] = {0, 1};
+    int mode = gf2x::tune_pinned(ctx, gf2x::TUNE_BATCH_PERSIST, modes, 2, -1);
+    if (mode < 0)
+        mode = gf2x::tune_choice(ctx, gf2x::TUNE_BATCH_PERSIST,
+                                 (gf2x::tune_bucket(bp.table.size()) << 8) | gf2x::tune_bucket(runs.size()), modes, 2,
+                                 0,
+                                 [&](int m) -> cudaError_t {
+                                     gf2x_status r2 = GF2X_OK;
+                                     if (m == 1) {
+                                         r2 = prepare_persistent(st);
+                                         if (r2 == GF2X_OK) r2 = from_cuda(gf2x::persist_launch(ctx, pl, st));
+                                     } else {
+                                         r2 = run_classes(st);
+                                     }
+                                     return r2 == GF2X_OK ? cudaSuccess : cudaErrorInvalidValue;
+                                 },
+                                 st);
+    const bool persistent = mode == 1 && prepare_persistent(st) == GF2X_OK;
+    auto run_all = [&](cudaStream_t s2) -> gf2x_status {
+        if (persistent) {
+            StageScope sc(ctx, STAGE_PERSIST, s2);
+            return from_cuda(gf2x::persist_launch(ctx, pl, s2));
+        }
+        return run_classes(s2);
     };
     // graph cache, keyed by the job table and the workspace (second call captures)
     BatchCache *bc = (BatchCache *)ctx->batch_graphs;

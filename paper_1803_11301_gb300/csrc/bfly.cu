@@ -298,4 +298,6 @@ cudaError_t butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 s
     return top_passes(ctx, x, nullptr, l, depth_or_default(bt, l), true, count, stride, st);
 }
 
+GF2X_OUT_OF_RANGE_READER(out_of_range_bfly)
+
 }  // namespace gf2x

@@ -98,7 +98,10 @@ __device__ __forceinline__ void bfly_top_body(const VBlock &vb, u64 *smem_raw, u
         const u64 base = (group << (p + M)) + col;
         u64 v[1 << M];
 #pragma unroll
-        for (int u = 0; u < (1 << M); ++u) v[u] = x[base + (u64)u * rstride];
+        for (int u = 0; u < (1 << M); ++u) {
+            const u64 i = base + (u64)u * rstride;
+            v[u] = in_range(i, 1ull << l) ? x[i] : 0;
+        }
 #pragma unroll
         for (int s2 = 0; s2 < M; ++s2) {
             const int r = INV ? s2 : M - 1 - s2;
@@ -118,7 +121,10 @@ __device__ __forceinline__ void bfly_top_body(const VBlock &vb, u64 *smem_raw, u
             }
         }
 #pragma unroll
-        for (int u = 0; u < (1 << M); ++u) x[base + (u64)u * rstride] = v[u];
+        for (int u = 0; u < (1 << M); ++u) {
+            const u64 i = base + (u64)u * rstride;
+            if (in_range(i, 1ull << l)) x[i] = v[u];
+        }
     }
 }
 
@@ -326,9 +332,10 @@ __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw
     const u64 base = (u64)vb.bx << bt;
     pdl_allow();
     pdl_wait();
+    const bool tile_ok = in_range(base + T - 1, 1ull << l);    // the tile lies in the transform
     for (int k = vb.t; k < T; k += vb.nt) {
-        a[k] = X[base + k];
-        if (fused) b[k] = Y[base + k];
+        a[k] = tile_ok ? X[base + k] : 0;
+        if (fused) b[k] = tile_ok ? Y[base + k] : 0;
     }
     u64 *ctops = tabs + CHUNK * kTab;                   // v_{l+32-i} + Cantor(base >> i), i < bt
     if (vb.t < bt) ctops[vb.t] = vcan[l + 32 - vb.t] ^ cantor(cvt, base >> vb.t);
@@ -338,6 +345,7 @@ __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw
         low_layers_regs(vb, a, b, bt, cvt, ctops, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
         vb.sync();
         if (mode != BOTTOM_FWD) table_layers<CHUNK>(vb, a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);
+        if (tile_ok)
         for (int k = vb.t; k < T; k += vb.nt) X[base + k] = a[k];
         return;
     }
@@ -363,7 +371,8 @@ __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw
         }
         table_layers<CHUNK>(vb, a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);
     }
-    for (int k = vb.t; k < T; k += vb.nt) X[base + k] = a[k];
+    if (tile_ok)
+        for (int k = vb.t; k < T; k += vb.nt) X[base + k] = a[k];
 }
 
 }  // namespace bflyk

@@ -143,6 +143,7 @@ __device__ __forceinline__ void cvt_wide_body(const VBlock &vb, u64 *bits, const
     if (4 * t >= words / 2) return;
     const u64 w = 4 * t;                          // index among all lo words
     const u64 seg = w >> hl, q0 = w & (hw - 1);
+    if (!in_range(seg * 2 * hw + 2 * hw - 1, words)) return;   // the thread's segment lies in the array
     if (src != bits) {
         const u64 *sp = src + seg * 2 * hw;
         u64 *op = bits + seg * 2 * hw;
@@ -223,6 +224,7 @@ __device__ __forceinline__ void cvt_tile_body(const VBlock &vb, u64 *sm, u64 *bi
     bits += (u64)vb.by * stride;
     src += (u64)vb.by * stride;
     const u64 tw = 1ull << P.tw_log;
+    if (!in_range((u64)vb.bx * tw + tw - 1, P.words)) return;   // the tile lies in the array
     u64 *g = bits + (u64)vb.bx * tw;
     const u64 *gs = src + (u64)vb.bx * tw;
     for (u64 w = vb.t; w < tw; w += vb.nt) copy_async8(sm + w, gs + w);
@@ -246,6 +248,7 @@ __device__ __forceinline__ void cvt_col_body(const VBlock &vb, u64 *sm, u64 *bit
     const u64 W = 1ull << wlog, S = 1ull << slog;
     const u64 cols = uw >> wlog;                        // column blocks per unit
     const u64 u0 = ((u64)vb.bx / cols) << slog, c0 = ((u64)vb.bx % cols) << wlog;
+    if (!in_range((u0 + S - 1) * uw + c0 + W - 1, P.words)) return;   // the block's units lie in the array
     for (u64 k = vb.t; k < S * W; k += vb.nt)
         copy_async8(sm + k, src + (u0 + (k >> wlog)) * uw + c0 + (k & (W - 1)));
     copy_async_wait();
@@ -387,6 +390,163 @@ __device__ __forceinline__ void cvt_taylor_body(const VBlock &vb, u64 *win, u64 
     for (int e = vb.t; e < G * W; e += vb.nt) {
         const int u = e >> lw, j = e & (W - 1);
         g[((u64)u << kUnitWordsLog) + c0 + j] = win[(halo + j) * CS + u];
+    }
+}
+
+// ------------------------------------------------- fused wide Taylor layers
+// F consecutive Taylor layers k_lo + F - 1 .. k_lo (forward order; the inverse
+// runs them k_lo .. k_lo + F - 1) at tau = 2^16 in one pass.  Layer k divides
+// every aligned segment of 2h = 2^(17+k) bits by x^h + x^d with h = 2^(16+k),
+// d = 2^k; with k >= 7 both are whole words: H_s = 2^(10+k) and D_s = 2^(k-6)
+// words at level s = k - k_lo.  A segment of the largest layer is 2^F rows of
+// H_0 = 2^(10+k_lo) words (row j: words [j H_0, (j+1) H_0) of the segment).
+// At level s rows with bit s of j clear are lo rows, the others hi rows; lo
+// row j takes from hi row j + 2^s (forward: hi' = hi with the quotient fix):
+//     lo[q] ^= hi'[q - D_s]   (for q < D_s: the end of hi row j + 2^s - 1, or
+//                              nothing when j is the first row of its half),
+//     fix: first hi row's words r < D_s ^= the last D_s words of its half's last row.
+// A block holds, for every row of one segment, the W columns [c0, c0 + W) it
+// writes and E = sum_s D_s columns to their left (every level reads D_s to the
+// left, so after all levels the W columns are exact); the block of c0 = 0
+// holds instead the last 2E columns of every row ("end rows", brought through
+// the same levels), from which it takes the quotient fixes and the reads that
+// cross into the previous row.  The halo columns and end rows are copied by a
+// pre-pass (wide_snap) before any block writes, so each block runs in place.
+
+struct WideGroup {
+    int F;            // layers in the group (2..4)
+    int klo;          // lowest layer
+    int inverse;
+    unsigned W;       // columns written per block
+    unsigned E;       // halo columns: D_min (2^F - 1)
+    u64 H0;           // words per row
+    u64 tiles;        // blocks per row: H0 / W
+    u64 segs;         // segments per job: words / (2^F H0)
+    u64 words;        // L / 64
+};
+
+// side buffer of one job: [segs][tiles][2^F rows][E] halos, then [segs][2^F rows][2E] end rows
+__device__ __forceinline__ u64 *wide_halo(u64 *side, const WideGroup &G, u64 seg, u64 t, int row)
+{
+    return side + ((seg * G.tiles + t) << G.F) * G.E + (u64)row * G.E;
+}
+
+__device__ __forceinline__ u64 *wide_end(u64 *side, const WideGroup &G, u64 seg, int row)
+{
+    return side + ((G.segs * G.tiles) << G.F) * G.E + ((seg << G.F) + (u64)row) * 2 * G.E;
+}
+
+// The pre-pass: block (seg, t) of job y copies its halo (t > 0) or the end rows (t = 0).
+__device__ __forceinline__ void wide_snap_body(const VBlock &vb, const u64 *bits, u64 *side, const WideGroup &G,
+                                               u64 stride)
+{
+    bits += (u64)vb.by * stride;
+    side += (u64)vb.by * stride;
+    const u64 seg = vb.bx / G.tiles, t = vb.bx % G.tiles;
+    const int R = 1 << G.F;
+    const u64 base = seg * ((u64)R * G.H0);
+    if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
+    if (t > 0) {
+        for (u64 k = vb.t; k < (u64)R * G.E; k += vb.nt) {
+            const int row = (int)(k / G.E);
+            const u64 i = k % G.E;
+            wide_halo(side, G, seg, t, row)[i] = bits[base + (u64)row * G.H0 + t * G.W - G.E + i];
+        }
+    } else {
+        for (u64 k = vb.t; k < (u64)R * 2 * G.E; k += vb.nt) {
+            const int row = (int)(k / (2 * G.E));
+            const u64 i = k % (2 * G.E);
+            wide_end(side, G, seg, row)[i] = bits[base + (u64)row * G.H0 + G.H0 - 2 * G.E + i];
+        }
+    }
+}
+
+// The fused pass, in place on bits.  sm: 2^F (E + W) words of rows, then (for
+// the block of c0 = 0) 2^F 2E words of end rows.
+__device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *bits, u64 *side, const WideGroup &G,
+                                                u64 stride)
+{
+    bits += (u64)vb.by * stride;
+    side += (u64)vb.by * stride;
+    const u64 seg = vb.bx / G.tiles, t = vb.bx % G.tiles;
+    const int R = 1 << G.F;
+    const unsigned E = G.E, W = G.W, RS = E + W;          // row stride in shared memory
+    const u64 base = seg * ((u64)R * G.H0), c0 = t * W;
+    if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
+    u64 *end = sm + (u64)R * RS;
+    // rows: columns x in [-E, W) at sm[row RS + E + x]
+    for (u64 k = vb.t; k < (u64)R * W; k += vb.nt) {
+        const int row = (int)(k / W);
+        const unsigned x = (unsigned)(k % W);
+        sm[row * RS + E + x] = bits[base + (u64)row * G.H0 + c0 + x];
+    }
+    if (t > 0) {
+        for (u64 k = vb.t; k < (u64)R * E; k += vb.nt) {
+            const int row = (int)(k / E);
+            const unsigned i = (unsigned)(k % E);
+            sm[row * RS + i] = wide_halo(side, G, seg, t, row)[i];
+        }
+    } else {
+        for (u64 k = vb.t; k < (u64)R * 2 * E; k += vb.nt) {
+            const int row = (int)(k / (2 * E));
+            const unsigned i = (unsigned)(k % (2 * E));
+            end[row * 2 * E + i] = wide_end(side, G, seg, row)[i];
+        }
+    }
+    vb.sync();
+    const unsigned Dmin = 1u << (G.klo - 6);
+    unsigned consumed = 0;                                   // sum of D over the levels run so far
+    for (int it = 0; it < G.F; ++it) {
+        const int s = G.inverse ? it : G.F - 1 - it;
+        const unsigned D = Dmin << s;
+        const int half = 1 << s;
+        consumed += D;
+        auto fix = [&]() {                                   // block of c0 = 0: first hi rows, words r < D
+            if (t != 0) return;
+            for (u64 k = vb.t; k < (u64)(R / 2) * D; k += vb.nt) {
+                const int h = (int)(k / D);                  // the h-th hi half
+                const unsigned r = (unsigned)(k % D);
+                const int jf = ((h >> s) << (s + 1)) + half; // first row of that hi half (h < R/2: h = seg index * half...)
+                if ((h & (half - 1)) != 0) continue;
+                sm[jf * RS + E + r] ^= end[(jf + half - 1) * 2 * E + 2 * E - D + r];
+            }
+        };
+        if (!G.inverse) {
+            fix();
+            vb.sync();
+        }
+        // lo update of the rows: x from the valid bound (t > 0) or 0 (t = 0) to W
+        const int xlo = t > 0 ? -(int)E + (int)consumed : 0;
+        const unsigned ncols = (unsigned)((int)W - xlo);
+        for (u64 k = vb.t; k < (u64)(R / 2) * ncols; k += vb.nt) {
+            const int lh = (int)(k / ncols);                 // the lh-th lo row
+            const int x = xlo + (int)(k % ncols);
+            const int j = ((lh >> s) << (s + 1)) | (lh & (half - 1));
+            const int jp = j + half;
+            u64 v = 0;
+            if (t > 0 || x - (int)D >= 0) v = sm[jp * RS + E + x - (int)D];
+            else if ((j & (half - 1)) != 0) v = end[(jp - 1) * 2 * E + 2 * E + x - (int)D];
+            sm[j * RS + E + x] ^= v;
+        }
+        if (t == 0) {                                        // the end rows through the same level
+            const unsigned nend = 2 * E - consumed;
+            for (u64 k = vb.t; k < (u64)(R / 2) * nend; k += vb.nt) {
+                const int lh = (int)(k / nend);
+                const unsigned i = consumed + (unsigned)(k % nend);
+                const int j = ((lh >> s) << (s + 1)) | (lh & (half - 1));
+                end[j * 2 * E + i] ^= end[(j + half) * 2 * E + i - D];
+            }
+        }
+        vb.sync();
+        if (G.inverse) {
+            fix();
+            vb.sync();
+        }
+    }
+    for (u64 k = vb.t; k < (u64)R * W; k += vb.nt) {
+        const int row = (int)(k / W);
+        const unsigned x = (unsigned)(k % W);
+        bits[base + (u64)row * G.H0 + c0 + x] = sm[row * RS + E + x];
     }
 }
 

@@ -135,4 +135,6 @@ cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int 
     return basis_cvt_unit16_r(ctx, bits, L, inverse, count, stride, R, st);
 }
 
+GF2X_OUT_OF_RANGE_READER(out_of_range_cvt_reg)
+
 }  // namespace gf2x

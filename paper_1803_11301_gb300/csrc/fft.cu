@@ -300,4 +300,6 @@ cudaError_t store_jobs(gf2x_ctx *ctx, const u64 *src, u64 stride, const JobDev *
     return cudaGetLastError();
 }
 
+GF2X_OUT_OF_RANGE_READER(out_of_range_fft)
+
 }  // namespace gf2x

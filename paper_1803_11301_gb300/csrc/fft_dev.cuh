@@ -60,7 +60,8 @@ __device__ __forceinline__ void encode_body(const VBlock &vb, u64 *tab, u64 *til
         vb.sync();
         for (int k = vb.t; k < 64 * cols; k += vb.nt) {
             const int j = k / cols, w = k % cols;
-            tile[j * kPad + w] = j < rows ? novel[(u64)j * rw + w0 + w] : 0;
+            const u64 src = (u64)j * rw + w0 + w;
+            tile[j * kPad + w] = (j < rows && in_range(src, 64 * rw)) ? novel[src] : 0;
         }
         copy_async_wait();
         vb.sync();
@@ -68,8 +69,10 @@ __device__ __forceinline__ void encode_body(const VBlock &vb, u64 *tab, u64 *til
             u64 A = tile[lane * kPad + w], B = tile[(lane + 32) * kPad + w];
             transpose64(A, B, lane);
             const u64 base = (w0 + w) * 64;
-            f[base + lane] = lin64(tab, A);
-            f[base + lane + 32] = lin64(tab, B);
+            if (in_range(base + 63, 64 * rw)) {
+                f[base + lane] = lin64(tab, A);
+                f[base + lane + 32] = lin64(tab, B);
+            }
         }
     }
 }
@@ -113,7 +116,8 @@ __device__ __forceinline__ void decode_body(const VBlock &vb, u64 *tab, u64 *til
         const u64 w0 = g * cols;
         for (int w = warp; w < cols; w += vb.nt >> 5) {
             const u64 base = (w0 + w) * 64;
-            u64 A = lin64(tab, h[base + lane]), B = lin64(tab, h[base + lane + 32]);
+            const bool ok = in_range(base + 63, 64 * rw);
+            u64 A = ok ? lin64(tab, h[base + lane]) : 0, B = ok ? lin64(tab, h[base + lane + 32]) : 0;
             transpose64(A, B, lane);
             tile[lane * kPad + w] = A;
             tile[(lane + 32) * kPad + w] = B;
@@ -121,7 +125,8 @@ __device__ __forceinline__ void decode_body(const VBlock &vb, u64 *tab, u64 *til
         vb.sync();
         for (int k = vb.t; k < 64 * cols; k += vb.nt) {
             const int j = k / cols, w = k % cols;
-            novel[(u64)j * rw + w0 + w] = tile[j * kPad + w];
+            const u64 dst = (u64)j * rw + w0 + w;
+            if (in_range(dst, 64 * rw)) novel[dst] = tile[j * kPad + w];
         }
         vb.sync();
     }

@@ -136,6 +136,45 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
     }
 }
 
+// ------------------------------------------------------ debug bounds checks
+// Built with GF2X_DEBUG_BOUNDS, the kernels check their main global indices
+// against the extent of the buffer they address: an index out of range is
+// counted (per source file) and its access skipped, never trapped;
+// gf2x_stream_status then reports GF2X_EBOUNDS.  Without the flag in_range
+// is true and costs nothing.
+#ifdef GF2X_DEBUG_BOUNDS
+static __device__ unsigned long long g_gf2x_out_of_range;
+#endif
+__device__ __forceinline__ bool in_range(u64 i, u64 extent)
+{
+#ifdef GF2X_DEBUG_BOUNDS
+    if (i >= extent) {
+        atomicAdd(&g_gf2x_out_of_range, 1ull);
+        return false;
+    }
+#else
+    (void)i;
+    (void)extent;
+#endif
+    return true;
+}
+
+// Each file with kernels defines its reader of the counter (host side):
+// returns it and resets it to zero; 0 in builds without the checks.
+#ifdef GF2X_DEBUG_BOUNDS
+#define GF2X_OUT_OF_RANGE_READER(name)                                                        \
+    unsigned long long name()                                                                 \
+    {                                                                                         \
+        unsigned long long h = 0, z = 0;                                                      \
+        if (cudaMemcpyFromSymbol(&h, g_gf2x_out_of_range, sizeof h) != cudaSuccess) return 0; \
+        if (h) cudaMemcpyToSymbol(g_gf2x_out_of_range, &z, sizeof z);                         \
+        return h;                                                                             \
+    }
+#else
+#define GF2X_OUT_OF_RANGE_READER(name) \
+    unsigned long long name() { return 0; }
+#endif
+
 // ------------------------------------------------------------ block bodies
 // The block a kernel body runs as: the launch's own block, or one sub-block of
 // the persistent batch kernel (persist.cu), which runs the blocks of many
@@ -420,6 +459,14 @@ cudaError_t m128_butterfly_bottom_fused(gf2x_ctx *ctx, u64 *X, const u64 *Y, int
 cudaError_t m128_butterfly_top_inverse(gf2x_ctx *ctx, u64 *x, int l, int count, u64 stride, cudaStream_t st,
                                        int bt = -1);
 cudaError_t m128_pointwise(gf2x_ctx *ctx, const u64 *a, const u64 *b, u64 *c, u64 count, cudaStream_t st);
+
+// Out-of-range indices the kernels of each file met since the last call
+// (GF2X_DEBUG_BOUNDS builds; 0 otherwise).
+unsigned long long out_of_range_fft();
+unsigned long long out_of_range_cvt();
+unsigned long long out_of_range_cvt_reg();
+unsigned long long out_of_range_bfly();
+unsigned long long out_of_range_persist();
 
 // gf2x_mul (same arguments and checks) with every kernel launched directly,
 // never through the CUDA graph cache (api.cu).

@@ -112,6 +112,7 @@ struct __align__(16) PSeg {
     unsigned g;           // blocks each sub-block runs per item: an item is q g blocks
     unsigned per_job;     // blocks of one job
     unsigned nvb;         // blocks of the launch
+    unsigned vbase, vend; // the blocks this queue entry covers (the whole launch)
     unsigned item0;       // its first item in the queue
     int prev;             // the segment it follows in its class, or -1
     unsigned done_off;    // its per-job completion counters
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistBlocksPerSM)
         __syncthreads();
         const PSeg &S = s_pseg;
         const unsigned q = S.q, per_item = q * S.g;
-        const unsigned v0 = (s_item - S.item0) * per_item, v1 = min(v0 + per_item, S.nvb);
+        const unsigned v0 = S.vbase + (s_item - S.item0) * per_item, v1 = min(v0 + per_item, S.vend);
         if (threadIdx.x == 0) {
             int go = 1;
             if (S.prev >= 0) {
@@ -366,8 +367,9 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: far above a
 // that depends on those counts only.
 size_t persist_area_bytes(size_t classes, size_t jobs)
 {
-    const size_t segs = classes * kPersistMaxSegs;
-    return 256 + segs * sizeof(PSeg) + classes * kPersistMaxPlanBytes + (size_t)kPersistMaxSegs * jobs * 4 + 256;
+    const size_t segs = classes * kPersistMaxSegs;       // queue entries: one per recorded launch
+    return 256 + segs * sizeof(PSeg) + 256 + classes * (kPersistMaxPlanBytes + 256) + (size_t)kPersistMaxSegs * jobs * 4 +
+           256;
 }
 
 size_t persist_seg_bytes() { return sizeof(PSeg); }
@@ -387,31 +389,27 @@ cudaError_t persist_prepare(gf2x_ctx *ctx, const Recorder *const *recs, int C, v
     std::vector<int> order((size_t)C);
     for (int c = 0; c < C; ++c) order[(size_t)c] = c;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[(size_t)x] > work[(size_t)y]; });
-    size_t total_segs = 0;
-    for (int c = 0; c < C; ++c) total_segs += (size_t)recs[c]->nseg;
+    // device area: [state 256][queue entries][plans of every class][per-job counters]
     char *base = (char *)area;
     const size_t off_state = 0, off_segs = 256;
-    const size_t off_blob = off_segs + ((total_segs * sizeof(PSeg) + 255) & ~(size_t)255);
-    std::vector<size_t> blob_at((size_t)C, 0);
-    size_t off_done = off_blob;
+    std::vector<size_t> blob_rel((size_t)C, 0);           // plans, relative to the plans' start
+    size_t blob_total = 0;
     for (int c = 0; c < C; ++c) {
-        blob_at[(size_t)c] = off_done;
-        off_done += (recs[c]->blob_bytes + 255) & ~(size_t)255;
+        blob_rel[(size_t)c] = blob_total;
+        blob_total += (recs[c]->blob_bytes + 255) & ~(size_t)255;
     }
-    std::vector<PSeg> ps;
-    ps.reserve(total_segs);
-    std::vector<int> next((size_t)C, 0), last((size_t)C, -1);
-    unsigned items = 0, counters = 0;
-    for (bool more = true; more;) {
-        more = false;
-        for (int c : order) {
-            const Recorder *R = recs[c];
-            if (next[(size_t)c] >= R->nseg) continue;
-            more = true;
-            const SegRec &r = R->segs[next[(size_t)c]++];
+    // the segments as the persistent kernel runs them, one per recorded launch
+    std::vector<PSeg> segs_all;
+    std::vector<std::vector<int>> seg_of((size_t)C);
+    unsigned counters = 0;
+    for (int c = 0; c < C; ++c) {
+        const Recorder *R = recs[c];
+        int prev = -1;
+        for (int k = 0; k < R->nseg; ++k) {
+            const SegRec &r = R->segs[k];
             PSeg p{};
             p.kind = r.kind;
-            for (int k = 0; k < 4; ++k) p.i[k] = r.i[k];
+            for (int t = 0; t < 4; ++t) p.i[t] = r.i[t];
             p.gx = r.gx;
             p.gy = r.gy;
             p.threads = r.threads;
@@ -422,33 +420,54 @@ cudaError_t persist_prepare(gf2x_ctx *ctx, const Recorder *const *recs, int C, v
             while (q > 1 && ((size_t)q * p.slice + p.plan_words) * 8 > kPersistSmem) --q;
             p.q = q;
             p.per_job = r.per_job;
-            // blocks per sub-block and item: up to 8, while every job still spans at least 4 items
-            unsigned g = 1;
-            while (g < 8 && 8 * g * q <= r.per_job) g *= 2;
-            p.g = g;
             p.nvb = r.gx * r.gy;
-            p.item0 = items;
-            items += (p.nvb + q * g - 1) / (q * g);
-            p.prev = last[(size_t)c];
+            p.prev = prev;
             p.done_off = counters;
-            if (p.prev >= 0) {
-                p.prev_done_off = ps[(size_t)p.prev].done_off;
-                p.prev_per_job = ps[(size_t)p.prev].per_job;
+            if (prev >= 0) {
+                p.prev_done_off = segs_all[(size_t)prev].done_off;
+                p.prev_per_job = segs_all[(size_t)prev].per_job;
             }
             counters += (unsigned)R->jobs;
-            p.plan = r.blob >= 0 ? (const void *)(base + blob_at[(size_t)c] + (size_t)r.blob) : nullptr;
-            for (int k = 0; k < 10; ++k) p.a[k] = r.a[k];
-            last[(size_t)c] = (int)ps.size();
+            // the plan's offset among the plans plus one, made an address once the layout is known
+            p.plan = r.blob >= 0 ? (const void *)(uintptr_t)(1 + blob_rel[(size_t)c] + (size_t)r.blob) : nullptr;
+            for (int t = 0; t < 10; ++t) p.a[t] = r.a[t];
+            prev = (int)segs_all.size();
+            seg_of[(size_t)c].push_back(prev);
+            segs_all.push_back(p);
+        }
+    }
+    // the queue: segments of the classes round robin (the class with most block-threads first)
+    std::vector<PSeg> ps;
+    std::vector<size_t> next((size_t)C, 0);
+    unsigned items = 0;
+    for (bool more = true; more;) {
+        more = false;
+        for (int c : order) {
+            if (next[(size_t)c] >= seg_of[(size_t)c].size()) continue;
+            more = true;
+            PSeg p = segs_all[(size_t)seg_of[(size_t)c][next[(size_t)c]++]];
+            // blocks per sub-block and item: up to 8, while every job still spans at least 4 items
+            unsigned g = 1;
+            while (g < 8 && 8 * g * p.q <= p.per_job) g *= 2;
+            p.g = g;
+            p.vbase = 0;
+            p.vend = p.nvb;
+            p.item0 = items;
+            items += (p.nvb + p.q * g - 1) / (p.q * g);
             ps.push_back(p);
         }
     }
+    const size_t off_blob = off_segs + ((ps.size() * sizeof(PSeg) + 255) & ~(size_t)255);
+    const size_t off_done = off_blob + blob_total;
+    for (PSeg &p : ps)
+        if (p.plan) p.plan = base + off_blob + ((uintptr_t)p.plan - 1);
     const size_t need = off_done + (size_t)counters * 4;
     if (need > area_bytes || ps.empty() || items == 0) return cudaErrorInvalidValue;
     e = cudaMemcpyAsync(base + off_segs, ps.data(), ps.size() * sizeof(PSeg), cudaMemcpyHostToDevice, st);
     for (int c = 0; c < C && e == cudaSuccess; ++c)
         if (recs[c]->blob_bytes)
-            e = cudaMemcpyAsync(base + blob_at[(size_t)c], recs[c]->blob, recs[c]->blob_bytes, cudaMemcpyHostToDevice,
-                                st);
+            e = cudaMemcpyAsync(base + off_blob + blob_rel[(size_t)c], recs[c]->blob, recs[c]->blob_bytes,
+                                cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, kPersistThreads, kPersistSmem);
@@ -492,6 +511,7 @@ cudaError_t persist_selftest_timeout(gf2x_ctx *ctx, cudaStream_t st, unsigned lo
         ps[k].threads = kPersistThreads;
         ps[k].q = 1;
         ps[k].nvb = 1;
+        ps[k].vend = 1;
         ps[k].item0 = (unsigned)k;
         ps[k].done_off = (unsigned)k;
     }
@@ -518,5 +538,7 @@ bool persist_supported(const Recorder &r)
         if (!supported(r.segs[k])) return false;
     return true;
 }
+
+GF2X_OUT_OF_RANGE_READER(out_of_range_persist)
 
 }  // namespace gf2x

@@ -105,7 +105,7 @@ class Server:
         self.rejected: list = []
         self.cancelled: list = []
         self._next_batch = 0
-        # resident transforms: key (b pointer, nb, n) -> tensor; counts of recurrences
+        # resident transforms: key (b_key, nb, n) -> (transform, its event, its stream); recurrence counts
         self.reuse_after = reuse_after      # 0: never keep transforms
         self.transform_budget = int(self.budget * transform_share)
         self.transforms: collections.OrderedDict = collections.OrderedDict()
@@ -134,10 +134,11 @@ class Server:
             self.rejected.append(req)
             return GF2X_ENOMEM
         nc = product_bits(req.na, req.nb)
-        if req.host:
-            req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64).pin_memory()
-        else:
-            req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64, device=self.device)
+        if req.out is None or req.out.numel() < max(_words(nc), 1):     # else the caller's buffer
+            if req.host:
+                req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64, pin_memory=True)
+            else:
+                req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64, device=self.device)
         req.state = "pending"
         self.pending.append(req)
         return GF2X_OK
@@ -208,6 +209,8 @@ class Server:
                 for r in bt.reqs:
                     r.done = now
                     r.state = "done"
+                    if r.host:                          # the device copies are no longer needed
+                        r._dev_a = r._dev_b = r._dev_out = None
                     self.completed.append(r)
                 finished += len(bt.reqs)
                 self.in_use -= bt.bytes
