@@ -959,12 +959,13 @@ static_assert(GF2X_KNOB_UNIT16_R == gf2x::TUNE_UNIT16_R && GF2X_KNOB_BOTTOM_SHAP
                   GF2X_KNOB_M128_BOTTOM_CHUNK == gf2x::TUNE_M128_BOTTOM_CHUNK &&
                   GF2X_KNOB_BOTTOM_DEPTH == gf2x::TUNE_BFLY_DEPTH &&
                   GF2X_KNOB_M128_BOTTOM_DEPTH == gf2x::TUNE_M128_BFLY_DEPTH &&
-                  GF2X_KNOB_BATCH_PERSISTENT == gf2x::TUNE_BATCH_PERSIST,
+                  GF2X_KNOB_BATCH_PERSISTENT == gf2x::TUNE_BATCH_PERSIST &&
+                  GF2X_KNOB_BOTTOM_MUL == gf2x::TUNE_BOTTOM_MUL,
               "the ABI's knob numbers are the tuner's");
 
 gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice)
 {
-    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_BATCH_PERSISTENT || choice < -1) return GF2X_EINVAL;
+    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_BOTTOM_MUL || choice < -1) return GF2X_EINVAL;
     gf2x::tuner_pin(ctx->tuner, knob, choice);
     ++graphs(ctx)->gen;           // captured graphs keep their shapes: capture again
     return GF2X_OK;

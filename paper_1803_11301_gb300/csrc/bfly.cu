@@ -43,13 +43,13 @@ __global__ void __launch_bounds__(kThreads) k_bfly_top(u64 *x0, u64 *x1, int l, 
     bfly_top_body<M, INV>(launch_block(), smem_raw, x0, x1, l, p, chunks, per_block, cvt, vcan, arrays, stride);
 }
 
-template <int THREADS, int CHUNK>
+template <int THREADS, int CHUNK, bool H4>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
     k_bfly_bottom(u64 *X, u64 *Y, int l, int bt, const u64 *__restrict__ cvt, const u64 *__restrict__ vcan, int mode,
                   u64 stride)
 {
     extern __shared__ u64 smem_raw[];
-    bfly_bottom_body<CHUNK>(launch_block(), smem_raw, X, Y, l, bt, cvt, vcan, mode, stride);
+    bfly_bottom_body<CHUNK, H4>(launch_block(), smem_raw, X, Y, l, bt, cvt, vcan, mode, stride);
 }
 
 size_t bottom_smem(int bt, bool fused, int chunk)
@@ -68,9 +68,20 @@ constexpr int kBottomThreadsLarge = 256, kBottomChunkLarge = 16;
 // at 2^11-point tiles, 4 blocks per SM; more build rounds, more warps).
 constexpr int kBottomChunkLean = 8;
 
-// shape 1: the small-count shape, 0: the large-count one, 2: the lean one
+template <int THREADS, int CHUNK>
+cudaError_t launch_bottom_kernel(bool pdl, int mul, dim3 grid, size_t smem, cudaStream_t st, u64 *X, u64 *Y, int l,
+                                 int bt, const u64 *cvt, const u64 *vcan, int mode, u64 stride)
+{
+    if (mul) return launch_pdl(pdl, k_bfly_bottom<THREADS, CHUNK, true>, grid, dim3(THREADS), smem, st, X, Y, l, bt, cvt,
+                               vcan, mode, stride);
+    return launch_pdl(pdl, k_bfly_bottom<THREADS, CHUNK, false>, grid, dim3(THREADS), smem, st, X, Y, l, bt, cvt, vcan,
+                      mode, stride);
+}
+
+// shape 1: the small-count shape, 0: the large-count one, 2: the lean one;
+// mul 0: the 16-bit integer product form, 1: the 32-bit one (gf64_mul_t)
 cudaError_t launch_bottom_shape(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int count, u64 stride,
-                                int shape, cudaStream_t st)
+                                int shape, int mul, cudaStream_t st)
 {
     const bool fused = mode == BOTTOM_FUSED || mode == BOTTOM_FUSED_PRE;
     const dim3 grid((unsigned)(1ull << (l - bt)), count);
@@ -84,17 +95,20 @@ cudaError_t launch_bottom_shape(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, in
     }
     cudaError_t e;
     if (shape == 1)
-        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall>, grid, dim3(kBottomThreadsSmall),
-                       bottom_smem(bt, fused, kBottomChunkSmall), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
-                       stride);
+        e = launch_bottom_kernel<kBottomThreadsSmall, kBottomChunkSmall>(ctx->pdl, mul, grid,
+                                                                         bottom_smem(bt, fused, kBottomChunkSmall), st,
+                                                                         X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                                                                         stride);
     else if (shape == 2)
-        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean>, grid, dim3(kBottomThreadsLarge),
-                       bottom_smem(bt, fused, kBottomChunkLean), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
-                       stride);
+        e = launch_bottom_kernel<kBottomThreadsLarge, kBottomChunkLean>(ctx->pdl, mul, grid,
+                                                                        bottom_smem(bt, fused, kBottomChunkLean), st, X,
+                                                                        Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                                                                        stride);
     else
-        e = launch_pdl(ctx->pdl, k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge>, grid, dim3(kBottomThreadsLarge),
-                       bottom_smem(bt, fused, kBottomChunkLarge), st, X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
-                       stride);
+        e = launch_bottom_kernel<kBottomThreadsLarge, kBottomChunkLarge>(ctx->pdl, mul, grid,
+                                                                         bottom_smem(bt, fused, kBottomChunkLarge), st,
+                                                                         X, Y, l, bt, ctx->d_cvt, ctx->d_cantor, mode,
+                                                                         stride);
     count_launch(ctx);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -107,13 +121,22 @@ void launch_bottom(gf2x_ctx *ctx, u64 *X, u64 *Y, int l, int bt, int mode, int c
     const u64 tiles = 1ull << (l - bt);
     int shape = tiles * (u64)count < 4 * (u64)ctx->num_sms ? 1 : 0;
     static const int cands[3] = {1, 0, 2};
-    if (!scratch) shape = tune_pinned(ctx, TUNE_BOTTOM_SHAPE, cands, 3, shape);
-    else {
-        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, (tune_bucket(tiles * (u64)count) << 2) | (u64)mode, cands, 3, shape,
-                            [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, st); },
+    static const int muls[2] = {0, 1};
+    int mul = 0;
+    const u64 key = (tune_bucket(tiles * (u64)count) << 2) | (u64)mode;
+    if (!scratch) {
+        shape = tune_pinned(ctx, TUNE_BOTTOM_SHAPE, cands, 3, shape);
+        mul = tune_pinned(ctx, TUNE_BOTTOM_MUL, muls, 2, mul);
+    } else {
+        // the block shape with the default product form, then the product form in that shape
+        shape = tune_choice(ctx, TUNE_BOTTOM_SHAPE, key, cands, 3, shape,
+                            [&](int sh) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, sh, 0, st); },
                             st);
+        mul = tune_choice(ctx, TUNE_BOTTOM_MUL, key | ((u64)shape << 40), muls, 2, 0,
+                          [&](int mv) { return launch_bottom_shape(ctx, scratch, Y, l, bt, mode, count, stride, shape, mv, st); },
+                          st);
     }
-    launch_bottom_shape(ctx, X, Y, l, bt, mode, count, stride, shape, st);
+    launch_bottom_shape(ctx, X, Y, l, bt, mode, count, stride, shape, mul, st);
 }
 
 template <int M, bool INV>
@@ -177,11 +200,17 @@ bool configured = false;
 void configure()
 {
     if (configured) return;
-    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall>,
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkSmall));
-    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge>,
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLarge));
-    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean>,
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLean));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsSmall, kBottomChunkSmall, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkSmall));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLarge, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLarge));
+    cudaFuncSetAttribute(k_bfly_bottom<kBottomThreadsLarge, kBottomChunkLean, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bottom_smem(kBottom, true, kBottomChunkLean));
     configured = true;
 }

@@ -136,6 +136,7 @@ enum BottomMode { BOTTOM_FWD = 0, BOTTOM_INV = 1, BOTTOM_FUSED = 2, BOTTOM_FUSED
 
 // One layer i (< bt) on a tile held in shared memory.  ctop = v_{l+32-i} +
 // Cantor((tile base) >> i); the block of local start s_lo adds Cantor(s_lo >> i).
+template <bool H4>
 __device__ __forceinline__ void tile_layer(const VBlock &vb, u64 *a, int bt, int i, u64 ctop, const u64 *__restrict__ cvt, bool inverse)
 {
     const int nb = 1 << (bt - 1);                       // butterflies per layer
@@ -146,11 +147,11 @@ __device__ __forceinline__ void tile_layer(const VBlock &vb, u64 *a, int bt, int
         u64 x0 = a[s0], x1 = a[s0 + span];
         u64 c = ctop ^ cvt[(blk << 1) & 255] ^ cvt[256 + ((blk << 1) >> 8)];   // Cantor(2 blk), 2 blk < 2^11
         if (!inverse) {
-            x0 ^= gf64_mul(c, x1);
+            x0 ^= gf64_mul_t<H4>(c, x1);
             x1 ^= x0;
         } else {
             x1 ^= x0;
-            x0 ^= gf64_mul(c, x1);
+            x0 ^= gf64_mul_t<H4>(c, x1);
         }
         a[s0] = x0;
         a[s0 + span] = x1;
@@ -264,7 +265,8 @@ __device__ __forceinline__ void pair_transition(u64 &x0, u64 &x1, int q, int lo)
 
 // Runs on every thread of the block; the tile holds 2^bt >= 64 points, so each
 // warp's 4 groups are all inside the tile or all outside (warp-uniform loop).
-static __device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, int bt, const u64 *__restrict__ cvt, const u64 *ctops, bool fwd,
+template <bool H4>
+__device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, int bt, const u64 *__restrict__ cvt, const u64 *ctops, bool fwd,
                                 bool fwd_b, bool fused, bool inv)
 {
     const int T = 1 << bt;
@@ -282,10 +284,10 @@ static __device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, i
             for (int i = 3; i >= 0; --i) {
                 const unsigned blk2 = (unsigned)((g0 + ins_bit(q, i, 0)) >> (i + 1)) << 1;   // 2 blk < 2^(bt-i)
                 const u64 c = ctops[i] ^ cvt[blk2 & 255] ^ cvt[256 + (blk2 >> 8)];   // twiddle top from shared memory
-                x0 ^= gf64_mul(c, x1);
+                x0 ^= gf64_mul_t<H4>(c, x1);
                 x1 ^= x0;
                 if (fwd_b) {
-                    y0 ^= gf64_mul(c, y1);
+                    y0 ^= gf64_mul_t<H4>(c, y1);
                     y1 ^= y0;
                 }
                 if (i > 0) {
@@ -295,8 +297,8 @@ static __device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, i
             }
         }
         if (fused) {                                       // pointwise step of Alg. 5
-            x0 = gf64_mul(x0, y0);
-            x1 = gf64_mul(x1, y1);
+            x0 = gf64_mul_t<H4>(x0, y0);
+            x1 = gf64_mul_t<H4>(x1, y1);
         }
         int last = 0;
         if (inv) {
@@ -305,7 +307,7 @@ static __device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, i
                 const unsigned blk2 = (unsigned)((g0 + ins_bit(q, i, 0)) >> (i + 1)) << 1;
                 const u64 c = ctops[i] ^ cvt[blk2 & 255] ^ cvt[256 + (blk2 >> 8)];   // twiddle top from shared memory
                 x1 ^= x0;
-                x0 ^= gf64_mul(c, x1);
+                x0 ^= gf64_mul_t<H4>(c, x1);
                 if (i < 3) pair_transition(x0, x1, q, i);
             }
             last = 3;
@@ -315,7 +317,8 @@ static __device__ void low_layers_regs(const VBlock &vb, u64 *a, const u64 *b, i
     }
 }
 
-template <int CHUNK>
+// H4: the integer form of the products of layers 0..3 and the pointwise step (gf64_mul_t).
+template <int CHUNK, bool H4 = false>
 __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw, u64 *X, u64 *Y, int l, int bt,
                                                  const u64 *__restrict__ cvt, const u64 *__restrict__ vcan, int mode,
                                                  u64 stride)
@@ -342,7 +345,7 @@ __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw
     vb.sync();
     if (bt >= 6) {                                      // layers 0..3 and the pointwise product in registers
         if (mode != BOTTOM_INV) table_layers<CHUNK>(vb, a, fwd_b ? b : nullptr, bt, cvt, ctops, tabs, false, false);
-        low_layers_regs(vb, a, b, bt, cvt, ctops, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
+        low_layers_regs<H4>(vb, a, b, bt, cvt, ctops, mode != BOTTOM_INV, fwd_b, fused, mode != BOTTOM_FWD);
         vb.sync();
         if (mode != BOTTOM_FWD) table_layers<CHUNK>(vb, a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);
         if (tile_ok)
@@ -355,18 +358,18 @@ __device__ __forceinline__ void bfly_bottom_body(const VBlock &vb, u64 *smem_raw
     if (mode != BOTTOM_INV) {
         table_layers<CHUNK>(vb, a, fwd_b ? b : nullptr, bt, cvt, ctops, tabs, false, false);
         for (int i = low - 1; i >= 0; --i) {
-            tile_layer(vb, a, bt, i, ctops[i], cvt, false);
-            if (fwd_b) tile_layer(vb, b, bt, i, ctops[i], cvt, false);
+            tile_layer<H4>(vb, a, bt, i, ctops[i], cvt, false);
+            if (fwd_b) tile_layer<H4>(vb, b, bt, i, ctops[i], cvt, false);
             vb.sync();
         }
     }
     if (fused) {
-        for (int k = vb.t; k < T; k += vb.nt) a[k] = gf64_mul(a[k], b[k]);   // pointwise step of Alg. 5
+        for (int k = vb.t; k < T; k += vb.nt) a[k] = gf64_mul_t<H4>(a[k], b[k]);   // pointwise step of Alg. 5
         vb.sync();
     }
     if (mode != BOTTOM_FWD) {
         for (int i = 0; i < low; ++i) {
-            tile_layer(vb, a, bt, i, ctops[i], cvt, true);
+            tile_layer<H4>(vb, a, bt, i, ctops[i], cvt, true);
             vb.sync();
         }
         table_layers<CHUNK>(vb, a, nullptr, bt, cvt, ctops, tabs, true, mode != BOTTOM_INV);

@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(kTaylorThreads) k_cvt_taylor(u64 *bits, const 
     cvt_taylor_body(launch_block(), win, bits, src, mw, W, inverse, stride);
 }
 
-__global__ void __launch_bounds__(256) k_wide_snap(const u64 *bits, u64 *side, WideGroup G, u64 stride)
+__global__ void __launch_bounds__(256) k_wide_snap(const u64 *__restrict__ bits, u64 *__restrict__ side, WideGroup G,
+                                                   u64 stride)
 {
     wide_snap_body(launch_block(), bits, side, G, stride);
 }
@@ -142,6 +143,9 @@ __global__ void k_wait_timeout_probe(GridSync *gs, int *status, unsigned long lo
 
 bool g_configured = false;
 constexpr size_t kWideSmemMax = 160 * 1024;       // shared memory of one fused wide block
+#ifndef GF2X_WIDE_FUSE_MAX
+#define GF2X_WIDE_FUSE_MAX 4                      // compile-time override to measure fewer layers per pass (1: none)
+#endif
 
 void configure_kernels()
 {
@@ -320,7 +324,7 @@ cudaError_t run_wide_layers(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, const
         // the longest run of consecutive layers from ks[k] (at most 4) whose block fits
         int F = 1;
         WideGroup G{};
-        for (int f = 4; f >= 2 && F == 1; --f) {
+        for (int f = GF2X_WIDE_FUSE_MAX; f >= 2 && F == 1; --f) {
             if (k + (size_t)f > ks.size() || recording(ctx) || !scratch) continue;
             bool consecutive = true;
             for (int i = 1; i < f; ++i) consecutive &= ks[k + i] == ks[k] + (inverse ? i : -i);

@@ -437,8 +437,8 @@ __device__ __forceinline__ u64 *wide_end(u64 *side, const WideGroup &G, u64 seg,
 }
 
 // The pre-pass: block (seg, t) of job y copies its halo (t > 0) or the end rows (t = 0).
-__device__ __forceinline__ void wide_snap_body(const VBlock &vb, const u64 *bits, u64 *side, const WideGroup &G,
-                                               u64 stride)
+__device__ __forceinline__ void wide_snap_body(const VBlock &vb, const u64 *__restrict__ bits, u64 *__restrict__ side,
+                                               const WideGroup &G, u64 stride)
 {
     bits += (u64)vb.by * stride;
     side += (u64)vb.by * stride;
@@ -446,23 +446,21 @@ __device__ __forceinline__ void wide_snap_body(const VBlock &vb, const u64 *bits
     const int R = 1 << G.F;
     const u64 base = seg * ((u64)R * G.H0);
     if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
-    if (t > 0) {
-        for (u64 k = vb.t; k < (u64)R * G.E; k += vb.nt) {
-            const int row = (int)(k / G.E);
-            const u64 i = k % G.E;
-            wide_halo(side, G, seg, t, row)[i] = bits[base + (u64)row * G.H0 + t * G.W - G.E + i];
-        }
-    } else {
-        for (u64 k = vb.t; k < (u64)R * 2 * G.E; k += vb.nt) {
-            const int row = (int)(k / (2 * G.E));
-            const u64 i = k % (2 * G.E);
-            wide_end(side, G, seg, row)[i] = bits[base + (u64)row * G.H0 + G.H0 - 2 * G.E + i];
+    for (int row = 0; row < R; ++row) {
+        const u64 *src = bits + base + (u64)row * G.H0;
+        if (t > 0) {
+            u64 *dst = wide_halo(side, G, seg, t, row);
+            for (unsigned i = vb.t; i < G.E; i += vb.nt) dst[i] = src[t * G.W - G.E + i];
+        } else {
+            u64 *dst = wide_end(side, G, seg, row);
+            for (unsigned i = vb.t; i < 2 * G.E; i += vb.nt) dst[i] = src[G.H0 - 2 * G.E + i];
         }
     }
 }
 
 // The fused pass, in place on bits.  sm: 2^F (E + W) words of rows, then (for
-// the block of c0 = 0) 2^F 2E words of end rows.
+// the block of c0 = 0) 2^F 2E words of end rows.  Loops run row by row with
+// 32-bit column indices (no divisions).
 __device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *bits, u64 *side, const WideGroup &G,
                                                 u64 stride)
 {
@@ -473,26 +471,22 @@ __device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *
     const unsigned E = G.E, W = G.W, RS = E + W;          // row stride in shared memory
     const u64 base = seg * ((u64)R * G.H0), c0 = t * W;
     if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
-    u64 *end = sm + (u64)R * RS;
-    // rows: columns x in [-E, W) at sm[row RS + E + x]
-    for (u64 k = vb.t; k < (u64)R * W; k += vb.nt) {
-        const int row = (int)(k / W);
-        const unsigned x = (unsigned)(k % W);
-        sm[row * RS + E + x] = bits[base + (u64)row * G.H0 + c0 + x];
-    }
-    if (t > 0) {
-        for (u64 k = vb.t; k < (u64)R * E; k += vb.nt) {
-            const int row = (int)(k / E);
-            const unsigned i = (unsigned)(k % E);
-            sm[row * RS + i] = wide_halo(side, G, seg, t, row)[i];
-        }
-    } else {
-        for (u64 k = vb.t; k < (u64)R * 2 * E; k += vb.nt) {
-            const int row = (int)(k / (2 * E));
-            const unsigned i = (unsigned)(k % (2 * E));
-            end[row * 2 * E + i] = wide_end(side, G, seg, row)[i];
+    u64 *end = sm + (unsigned)R * RS;
+    // rows: columns x in [-E, W) at sm[row RS + E + x]; asynchronous copies, so that a thread
+    // has all of its loads in flight before it waits
+    for (int row = 0; row < R; ++row) {
+        const u64 *src = bits + base + (u64)row * G.H0 + c0;
+        u64 *dst = sm + row * RS + E;
+        for (unsigned x = vb.t; x < W; x += vb.nt) copy_async8(dst + x, src + x);
+        if (t > 0) {
+            const u64 *h = wide_halo(side, G, seg, t, row);
+            for (unsigned i = vb.t; i < E; i += vb.nt) copy_async8(sm + row * RS + i, h + i);
+        } else {
+            const u64 *e = wide_end(side, G, seg, row);
+            for (unsigned i = vb.t; i < 2 * E; i += vb.nt) copy_async8(end + row * 2 * E + i, e + i);
         }
     }
+    copy_async_wait();
     vb.sync();
     const unsigned Dmin = 1u << (G.klo - 6);
     unsigned consumed = 0;                                   // sum of D over the levels run so far
@@ -503,38 +497,35 @@ __device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *
         consumed += D;
         auto fix = [&]() {                                   // block of c0 = 0: first hi rows, words r < D
             if (t != 0) return;
-            for (u64 k = vb.t; k < (u64)(R / 2) * D; k += vb.nt) {
-                const int h = (int)(k / D);                  // the h-th hi half
-                const unsigned r = (unsigned)(k % D);
-                const int jf = ((h >> s) << (s + 1)) + half; // first row of that hi half (h < R/2: h = seg index * half...)
-                if ((h & (half - 1)) != 0) continue;
-                sm[jf * RS + E + r] ^= end[(jf + half - 1) * 2 * E + 2 * E - D + r];
-            }
+            for (int jf = half; jf < R; jf += 2 * half)      // first row of every hi half
+                for (unsigned r = vb.t; r < D; r += vb.nt)
+                    sm[jf * RS + E + r] ^= end[(jf + half - 1) * 2 * E + 2 * E - D + r];
         };
         if (!G.inverse) {
             fix();
             vb.sync();
         }
-        // lo update of the rows: x from the valid bound (t > 0) or 0 (t = 0) to W
-        const int xlo = t > 0 ? -(int)E + (int)consumed : 0;
-        const unsigned ncols = (unsigned)((int)W - xlo);
-        for (u64 k = vb.t; k < (u64)(R / 2) * ncols; k += vb.nt) {
-            const int lh = (int)(k / ncols);                 // the lh-th lo row
-            const int x = xlo + (int)(k % ncols);
-            const int j = ((lh >> s) << (s + 1)) | (lh & (half - 1));
+        // lo update of the rows: columns from the valid bound (t > 0) or 0 (t = 0) to W
+        const unsigned xoff = t > 0 ? consumed : E;           // first column, as an offset in the row's storage
+        for (int j = 0; j < R; ++j) {
+            if (j & half) continue;                          // hi row at this level
             const int jp = j + half;
-            u64 v = 0;
-            if (t > 0 || x - (int)D >= 0) v = sm[jp * RS + E + x - (int)D];
-            else if ((j & (half - 1)) != 0) v = end[(jp - 1) * 2 * E + 2 * E + x - (int)D];
-            sm[j * RS + E + x] ^= v;
+            u64 *lo = sm + j * RS;
+            const u64 *hi = sm + jp * RS;
+            for (unsigned xs = xoff + vb.t; xs < RS; xs += vb.nt) {    // xs = E + x
+                u64 v;
+                if (t > 0 || xs >= E + D) v = hi[xs - D];
+                else if ((j & (half - 1)) != 0) v = end[(jp - 1) * 2 * E + E + xs - D];   // index 2E + x - D
+                else v = 0;
+                lo[xs] ^= v;
+            }
         }
         if (t == 0) {                                        // the end rows through the same level
-            const unsigned nend = 2 * E - consumed;
-            for (u64 k = vb.t; k < (u64)(R / 2) * nend; k += vb.nt) {
-                const int lh = (int)(k / nend);
-                const unsigned i = consumed + (unsigned)(k % nend);
-                const int j = ((lh >> s) << (s + 1)) | (lh & (half - 1));
-                end[j * 2 * E + i] ^= end[(j + half) * 2 * E + i - D];
+            for (int j = 0; j < R; ++j) {
+                if (j & half) continue;
+                u64 *lo = end + j * 2 * E;
+                const u64 *hi = end + (j + half) * 2 * E;
+                for (unsigned i = consumed + vb.t; i < 2 * E; i += vb.nt) lo[i] ^= hi[i - D];
             }
         }
         vb.sync();
@@ -543,10 +534,10 @@ __device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *
             vb.sync();
         }
     }
-    for (u64 k = vb.t; k < (u64)R * W; k += vb.nt) {
-        const int row = (int)(k / W);
-        const unsigned x = (unsigned)(k % W);
-        bits[base + (u64)row * G.H0 + c0 + x] = sm[row * RS + E + x];
+    for (int row = 0; row < R; ++row) {
+        u64 *dst = bits + base + (u64)row * G.H0 + c0;
+        const u64 *src = sm + row * RS + E;
+        for (unsigned x = vb.t; x < W; x += vb.nt) dst[x] = src[x];
     }
 }
 

@@ -47,14 +47,9 @@ __device__ __forceinline__ u32 clmul16(u32 a, u32 b)
     return (z0 & 0x49249249u) | (z1 & 0x12492492u) | (z2 & 0x24924924u);
 }
 
-// 32 x 32 -> 63 bits: Karatsuba over the 16-bit halves (GF2X_CLMUL32_H4 selects
-// the four-class form below at compile time, to measure one against the other).
-__device__ __forceinline__ u64 clmul32_h4(u32 a, u32 b);
+// 32 x 32 -> 63 bits: Karatsuba over the 16-bit halves.
 __device__ __forceinline__ u64 clmul32(u32 a, u32 b)
 {
-#ifdef GF2X_CLMUL32_H4
-    return clmul32_h4(a, b);
-#endif
     const u32 al = a & 0xFFFFu, ah = a >> 16, bl = b & 0xFFFFu, bh = b >> 16;
     const u32 lo = clmul16(al, bl), hi = clmul16(ah, bh);
     const u32 mid = clmul16(al ^ ah, bl ^ bh) ^ lo ^ hi;
@@ -63,8 +58,9 @@ __device__ __forceinline__ u64 clmul32(u32 a, u32 b)
 
 // 32 x 32 -> 63 bits with four classes (bit positions mod 4): at most 8 terms
 // per output position, a count that fits in 4 bits; sixteen 32 x 32 -> 64-bit
-// multiplies.  Slower than clmul32 but it needs fewer registers: the
-// GF(2^128) kernels (m128.cu), whose products hold twice the state, keep it.
+// multiplies.  Slower than clmul32 alone but it needs fewer registers: the
+// GF(2^128) kernels (m128.cu), whose products hold twice the state, keep it,
+// and the fused Butterfly kernel can take either (gf64_mul_t).
 __device__ __forceinline__ u64 clmul32_h4(u32 a, u32 b)
 {
     const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
@@ -87,14 +83,21 @@ __device__ __forceinline__ u64 gf64_reduce(u64 hi, u64 lo)
     return lo ^ t;
 }
 
-__device__ __forceinline__ u64 gf64_mul(u64 a, u64 b)
+// The GF(2^64) product with either integer form of the 32 x 32 carry-less
+// product: H4 = false, the 16-bit form (clmul32); H4 = true, the four-class
+// 32-bit form (clmul32_h4).  The same result; the fused Butterfly kernel lets
+// the tuner pick per launch shape.
+template <bool H4>
+__device__ __forceinline__ u64 gf64_mul_t(u64 a, u64 b)
 {
     u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
-    u64 lo = clmul32(al, bl);
-    u64 hi = clmul32(ah, bh);
-    u64 mid = clmul32(al ^ ah, bl ^ bh) ^ lo ^ hi;          // Karatsuba middle term
+    u64 lo = H4 ? clmul32_h4(al, bl) : clmul32(al, bl);
+    u64 hi = H4 ? clmul32_h4(ah, bh) : clmul32(ah, bh);
+    u64 mid = (H4 ? clmul32_h4(al ^ ah, bl ^ bh) : clmul32(al ^ ah, bl ^ bh)) ^ lo ^ hi;   // Karatsuba middle term
     return gf64_reduce(hi ^ (mid >> 32), lo ^ (mid << 32));
 }
+
+__device__ __forceinline__ u64 gf64_mul(u64 a, u64 b) { return gf64_mul_t<false>(a, b); }
 
 // 64-bit GF(2)-linear map given as 8 byte-window tables (t[k][v] = image of
 // v << 8k): the method of four Russians with 8-bit windows (Sec. 4.5).
@@ -362,7 +365,7 @@ namespace gf2x {
 // The same numbers as the GF2X_KNOB_* constants of the C ABI.
 enum TuneKnob {
     TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3, TUNE_M128_BOTTOM_CHUNK = 4, TUNE_BFLY_DEPTH = 5,
-    TUNE_M128_BFLY_DEPTH = 6, TUNE_BATCH_PERSIST = 7, TUNE_KNOB_END = 8
+    TUNE_M128_BFLY_DEPTH = 6, TUNE_BATCH_PERSIST = 7, TUNE_BOTTOM_MUL = 8, TUNE_KNOB_END = 9
 };
 void *tuner_create();
 void tuner_destroy(void *t);

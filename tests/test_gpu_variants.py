@@ -59,7 +59,7 @@ def test_pin_arguments(ctx):
     with pytest.raises(Gf2xError):
         ctx.tune_pin(0, 9)
     with pytest.raises(Gf2xError):
-        ctx.tune_pin(8, 9)
+        ctx.tune_pin(9, 9)
     with pytest.raises(Gf2xError):
         ctx.tune_pin(5, -2)
     ctx.tune_pin(5, -1)                                   # releasing an unpinned knob is fine
@@ -80,6 +80,23 @@ def test_product_every_bottom_depth_and_shape(ctx, pins, depth, shape):
             got = host(ctx.mul(da, na, db, nb))
             assert np.array_equal(got, want), (depth, shape, na, nb, rep)
         assert ctx.bottom_layers(na, nb) == depth
+
+
+@pytest.mark.parametrize("mul", [0, 1])
+@pytest.mark.parametrize("depth,shape", [(9, 0), (11, 1), (8, 2)])
+def test_product_both_integer_forms(ctx, pins, mul, depth, shape):
+    # the bottom kernel's integer layers and pointwise step with either product form
+    from paper_1803_11301_gb300 import KNOB_BOTTOM_DEPTH, KNOB_BOTTOM_MUL, KNOB_BOTTOM_SHAPE
+    pins(KNOB_BOTTOM_MUL, mul)
+    pins(KNOB_BOTTOM_DEPTH, depth)
+    pins(KNOB_BOTTOM_SHAPE, shape)
+    for na, nb in [(1 << 20, (1 << 20) - 3), (70001, 3333)]:
+        a = synth.operand(synth.config_seed(30, na + mul), na)
+        b = synth.operand(synth.config_seed(31, nb + mul), nb)
+        want = O.mul(a, na, b, nb)
+        da, db = dev(a), dev(b)
+        for rep in range(2):
+            assert np.array_equal(host(ctx.mul(da, na, db, nb)), want), (mul, depth, shape, na, nb, rep)
 
 
 @pytest.mark.parametrize("depth,shape", [(8, 1), (10, 2), (11, 0), (9, 1)])
