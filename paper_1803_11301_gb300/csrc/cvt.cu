@@ -120,20 +120,6 @@ __global__ void __launch_bounds__(kTaylorThreads) k_cvt_taylor(u64 *bits, const 
     cvt_taylor_body(launch_block(), win, bits, src, mw, W, inverse, stride);
 }
 
-__global__ void __launch_bounds__(256) k_wide_snap(const u64 *__restrict__ bits, u64 *__restrict__ side, WideGroup G,
-                                                   u64 stride)
-{
-    wide_snap_body(launch_block(), bits, side, G, stride);
-}
-
-constexpr int kWideThreads = 512;
-
-__global__ void __launch_bounds__(kWideThreads) k_wide_fused(u64 *bits, u64 *side, WideGroup G, u64 stride)
-{
-    extern __shared__ u64 sm[];
-    wide_fused_body(launch_block(), sm, bits, side, G, stride);
-}
-
 // Bounded-wait self-test: one block waits for a second arrival that never
 // comes, so the wait runs out and records GF2X_ETIMEOUT.
 __global__ void k_wait_timeout_probe(GridSync *gs, int *status, unsigned long long limit)
@@ -142,15 +128,10 @@ __global__ void k_wait_timeout_probe(GridSync *gs, int *status, unsigned long lo
 }
 
 bool g_configured = false;
-constexpr size_t kWideSmemMax = 160 * 1024;       // shared memory of one fused wide block
-#ifndef GF2X_WIDE_FUSE_MAX
-#define GF2X_WIDE_FUSE_MAX 4                      // compile-time override to measure fewer layers per pass (1: none)
-#endif
 
 void configure_kernels()
 {
     if (g_configured) return;
-    cudaFuncSetAttribute(k_wide_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideSmemMax);
     cudaFuncSetAttribute(k_cvt_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
     cudaFuncSetAttribute(k_cvt_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)8 << kTileWordsLog));
     cudaFuncSetAttribute(k_cvt_taylor, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -307,59 +288,6 @@ cudaError_t taylor_window_launch(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L
     return cudaGetLastError();
 }
 
-// The wide Taylor layers ks (at tau = 2^16, in the order they run: descending
-// for the forward conversion, ascending for the inverse) in as few HBM passes
-// as shared memory allows: runs of 2 to 4 consecutive layers as one fused pass
-// (a snapshot pre-pass, then the layers in place; the snapshots go to the
-// first part of `scratch`, a free buffer laid out like bits), single layers
-// as the one-step kernel.  While a launch is being recorded for the
-// persistent batch kernel every layer is a one-step kernel.
-cudaError_t run_wide_layers(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, const std::vector<int> &ks, bool inverse,
-                            int count, u64 stride, cudaStream_t st)
-{
-    configure_kernels();
-    const u64 words = L >> 6;
-    size_t k = 0;
-    while (k < ks.size()) {
-        // the longest run of consecutive layers from ks[k] (at most 4) whose block fits
-        int F = 1;
-        WideGroup G{};
-        for (int f = GF2X_WIDE_FUSE_MAX; f >= 2 && F == 1; --f) {
-            if (k + (size_t)f > ks.size() || recording(ctx) || !scratch) continue;
-            bool consecutive = true;
-            for (int i = 1; i < f; ++i) consecutive &= ks[k + i] == ks[k] + (inverse ? i : -i);
-            if (!consecutive) continue;
-            const int klo = inverse ? ks[k] : ks[k + f - 1];
-            if (klo < 7) continue;                       // shifts of whole words only
-            const u64 Dmin = 1ull << (klo - 6), E = Dmin * ((1ull << f) - 1), Dmax = Dmin << (f - 1);
-            u64 W = 256;
-            while (W < 4 * E || W < E + Dmax) W *= 2;
-            const u64 H0 = 1ull << (10 + klo);
-            const size_t smem = ((size_t)1 << f) * (E + W + 2 * E) * 8;
-            if (smem > kWideSmemMax || W > H0 || ((u64)1 << f) * H0 > words) continue;
-            F = f;
-            G = WideGroup{f, klo, inverse ? 1 : 0, (unsigned)W, (unsigned)E, H0, H0 / W, words / (((u64)1 << f) * H0),
-                          words};
-        }
-        if (F == 1) {
-            const u64 kk = (u64)ks[k];
-            TRY_CUDA(run_steps_generic(ctx, bits, bits, L, {Step{1ull << (16 + kk), 1ull << kk}}, inverse, count, stride,
-                                       st));
-            ++k;
-            continue;
-        }
-        const dim3 grid((unsigned)(G.segs * G.tiles), (unsigned)count);
-        const size_t smem = ((size_t)1 << F) * (G.E + G.W + 2 * G.E) * 8;
-        k_wide_snap<<<grid, 256, 0, st>>>(bits, scratch, G, stride);
-        count_launch(ctx);
-        k_wide_fused<<<grid, kWideThreads, smem, st>>>(bits, scratch, G, stride);
-        count_launch(ctx);
-        TRY_CUDA(cudaGetLastError());
-        k += (size_t)F;
-    }
-    return cudaSuccess;
-}
-
 // 18 <= K <= 32: Alg. 1 splits at tau = 2^16 with m = K - 16 >= 2:
 //   (a) Taylor expansion, steps (2^(16+k), 2^k) for k = m-1 .. 0: the low
 //       layers (up to 8) in the window kernel, the rest as wide steps;
@@ -398,15 +326,14 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
                           }, st);
     }
     const int mw = m < cap ? m : cap;
-    std::vector<Step> outer_taylor;
-    std::vector<int> wide_fwd, wide_inv;                  // wide Taylor layers in running order
-    for (int k = m - 1; k >= mw; --k) wide_fwd.push_back(k);
-    for (int k = mw; k <= m - 1; ++k) wide_inv.push_back(k);
+    std::vector<Step> taylor_wide, outer_taylor;
+    for (int k = m - 1; k >= mw; --k) taylor_wide.push_back({1ull << (16 + k), 1ull << k});
     if (m >= 10)
         for (int k = m - 9; k >= 0; --k) outer_taylor.push_back({1ull << (24 + k), 1ull << (16 + k)});
+    const std::vector<Step> taylor_wide_inv(taylor_wide.rbegin(), taylor_wide.rend());
     const std::vector<Step> outer_taylor_inv(outer_taylor.rbegin(), outer_taylor.rend());
     if (!inverse) {
-        TRY_CUDA(run_wide_layers(ctx, bits, scratch, L, wide_fwd, false, count, stride, st));
+        TRY_CUDA(run_steps_generic(ctx, bits, bits, L, taylor_wide, false, count, stride, st));
         TRY_CUDA(taylor_window_launch(ctx, scratch, bits, L, mw, false, count, stride, st));
         if (m <= 9) {
             TRY_CUDA(basis_cvt_outer(ctx, bits, scratch, L, m, kUnitWordsLog, false, count, stride, st));
@@ -426,7 +353,7 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
         TRY_CUDA(run_steps_generic(ctx, scratch, bits, L, outer_taylor_inv, true, count, stride, st));
     }
     TRY_CUDA(taylor_window_launch(ctx, bits, scratch, L, mw, true, count, stride, st));
-    return run_wide_layers(ctx, bits, scratch, L, wide_inv, true, count, stride, st);
+    return run_steps_generic(ctx, bits, bits, L, taylor_wide_inv, true, count, stride, st);
 }
 
 }  // namespace

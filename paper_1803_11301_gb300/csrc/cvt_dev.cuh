@@ -393,153 +393,5 @@ __device__ __forceinline__ void cvt_taylor_body(const VBlock &vb, u64 *win, u64 
     }
 }
 
-// ------------------------------------------------- fused wide Taylor layers
-// F consecutive Taylor layers k_lo + F - 1 .. k_lo (forward order; the inverse
-// runs them k_lo .. k_lo + F - 1) at tau = 2^16 in one pass.  Layer k divides
-// every aligned segment of 2h = 2^(17+k) bits by x^h + x^d with h = 2^(16+k),
-// d = 2^k; with k >= 7 both are whole words: H_s = 2^(10+k) and D_s = 2^(k-6)
-// words at level s = k - k_lo.  A segment of the largest layer is 2^F rows of
-// H_0 = 2^(10+k_lo) words (row j: words [j H_0, (j+1) H_0) of the segment).
-// At level s rows with bit s of j clear are lo rows, the others hi rows; lo
-// row j takes from hi row j + 2^s (forward: hi' = hi with the quotient fix):
-//     lo[q] ^= hi'[q - D_s]   (for q < D_s: the end of hi row j + 2^s - 1, or
-//                              nothing when j is the first row of its half),
-//     fix: first hi row's words r < D_s ^= the last D_s words of its half's last row.
-// A block holds, for every row of one segment, the W columns [c0, c0 + W) it
-// writes and E = sum_s D_s columns to their left (every level reads D_s to the
-// left, so after all levels the W columns are exact); the block of c0 = 0
-// holds instead the last 2E columns of every row ("end rows", brought through
-// the same levels), from which it takes the quotient fixes and the reads that
-// cross into the previous row.  The halo columns and end rows are copied by a
-// pre-pass (wide_snap) before any block writes, so each block runs in place.
-
-struct WideGroup {
-    int F;            // layers in the group (2..4)
-    int klo;          // lowest layer
-    int inverse;
-    unsigned W;       // columns written per block
-    unsigned E;       // halo columns: D_min (2^F - 1)
-    u64 H0;           // words per row
-    u64 tiles;        // blocks per row: H0 / W
-    u64 segs;         // segments per job: words / (2^F H0)
-    u64 words;        // L / 64
-};
-
-// side buffer of one job: [segs][tiles][2^F rows][E] halos, then [segs][2^F rows][2E] end rows
-__device__ __forceinline__ u64 *wide_halo(u64 *side, const WideGroup &G, u64 seg, u64 t, int row)
-{
-    return side + ((seg * G.tiles + t) << G.F) * G.E + (u64)row * G.E;
-}
-
-__device__ __forceinline__ u64 *wide_end(u64 *side, const WideGroup &G, u64 seg, int row)
-{
-    return side + ((G.segs * G.tiles) << G.F) * G.E + ((seg << G.F) + (u64)row) * 2 * G.E;
-}
-
-// The pre-pass: block (seg, t) of job y copies its halo (t > 0) or the end rows (t = 0).
-__device__ __forceinline__ void wide_snap_body(const VBlock &vb, const u64 *__restrict__ bits, u64 *__restrict__ side,
-                                               const WideGroup &G, u64 stride)
-{
-    bits += (u64)vb.by * stride;
-    side += (u64)vb.by * stride;
-    const u64 seg = vb.bx / G.tiles, t = vb.bx % G.tiles;
-    const int R = 1 << G.F;
-    const u64 base = seg * ((u64)R * G.H0);
-    if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
-    for (int row = 0; row < R; ++row) {
-        const u64 *src = bits + base + (u64)row * G.H0;
-        if (t > 0) {
-            u64 *dst = wide_halo(side, G, seg, t, row);
-            for (unsigned i = vb.t; i < G.E; i += vb.nt) dst[i] = src[t * G.W - G.E + i];
-        } else {
-            u64 *dst = wide_end(side, G, seg, row);
-            for (unsigned i = vb.t; i < 2 * G.E; i += vb.nt) dst[i] = src[G.H0 - 2 * G.E + i];
-        }
-    }
-}
-
-// The fused pass, in place on bits.  sm: 2^F (E + W) words of rows, then (for
-// the block of c0 = 0) 2^F 2E words of end rows.  Loops run row by row with
-// 32-bit column indices (no divisions).
-__device__ __forceinline__ void wide_fused_body(const VBlock &vb, u64 *sm, u64 *bits, u64 *side, const WideGroup &G,
-                                                u64 stride)
-{
-    bits += (u64)vb.by * stride;
-    side += (u64)vb.by * stride;
-    const u64 seg = vb.bx / G.tiles, t = vb.bx % G.tiles;
-    const int R = 1 << G.F;
-    const unsigned E = G.E, W = G.W, RS = E + W;          // row stride in shared memory
-    const u64 base = seg * ((u64)R * G.H0), c0 = t * W;
-    if (!in_range(base + (u64)R * G.H0 - 1, G.words)) return;
-    u64 *end = sm + (unsigned)R * RS;
-    // rows: columns x in [-E, W) at sm[row RS + E + x]; asynchronous copies, so that a thread
-    // has all of its loads in flight before it waits
-    for (int row = 0; row < R; ++row) {
-        const u64 *src = bits + base + (u64)row * G.H0 + c0;
-        u64 *dst = sm + row * RS + E;
-        for (unsigned x = vb.t; x < W; x += vb.nt) copy_async8(dst + x, src + x);
-        if (t > 0) {
-            const u64 *h = wide_halo(side, G, seg, t, row);
-            for (unsigned i = vb.t; i < E; i += vb.nt) copy_async8(sm + row * RS + i, h + i);
-        } else {
-            const u64 *e = wide_end(side, G, seg, row);
-            for (unsigned i = vb.t; i < 2 * E; i += vb.nt) copy_async8(end + row * 2 * E + i, e + i);
-        }
-    }
-    copy_async_wait();
-    vb.sync();
-    const unsigned Dmin = 1u << (G.klo - 6);
-    unsigned consumed = 0;                                   // sum of D over the levels run so far
-    for (int it = 0; it < G.F; ++it) {
-        const int s = G.inverse ? it : G.F - 1 - it;
-        const unsigned D = Dmin << s;
-        const int half = 1 << s;
-        consumed += D;
-        auto fix = [&]() {                                   // block of c0 = 0: first hi rows, words r < D
-            if (t != 0) return;
-            for (int jf = half; jf < R; jf += 2 * half)      // first row of every hi half
-                for (unsigned r = vb.t; r < D; r += vb.nt)
-                    sm[jf * RS + E + r] ^= end[(jf + half - 1) * 2 * E + 2 * E - D + r];
-        };
-        if (!G.inverse) {
-            fix();
-            vb.sync();
-        }
-        // lo update of the rows: columns from the valid bound (t > 0) or 0 (t = 0) to W
-        const unsigned xoff = t > 0 ? consumed : E;           // first column, as an offset in the row's storage
-        for (int j = 0; j < R; ++j) {
-            if (j & half) continue;                          // hi row at this level
-            const int jp = j + half;
-            u64 *lo = sm + j * RS;
-            const u64 *hi = sm + jp * RS;
-            for (unsigned xs = xoff + vb.t; xs < RS; xs += vb.nt) {    // xs = E + x
-                u64 v;
-                if (t > 0 || xs >= E + D) v = hi[xs - D];
-                else if ((j & (half - 1)) != 0) v = end[(jp - 1) * 2 * E + E + xs - D];   // index 2E + x - D
-                else v = 0;
-                lo[xs] ^= v;
-            }
-        }
-        if (t == 0) {                                        // the end rows through the same level
-            for (int j = 0; j < R; ++j) {
-                if (j & half) continue;
-                u64 *lo = end + j * 2 * E;
-                const u64 *hi = end + (j + half) * 2 * E;
-                for (unsigned i = consumed + vb.t; i < 2 * E; i += vb.nt) lo[i] ^= hi[i - D];
-            }
-        }
-        vb.sync();
-        if (G.inverse) {
-            fix();
-            vb.sync();
-        }
-    }
-    for (int row = 0; row < R; ++row) {
-        u64 *dst = bits + base + (u64)row * G.H0 + c0;
-        const u64 *src = sm + row * RS + E;
-        for (unsigned x = vb.t; x < W; x += vb.nt) dst[x] = src[x];
-    }
-}
-
 }  // namespace cvtk
 }  // namespace gf2x
