@@ -270,6 +270,10 @@ GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
  *   GF2X_KNOB_BOTTOM_MUL         the GF(2^64) products of the fused bottom kernel's
  *                                integer layers and pointwise step: 0 (16x16-bit integer
  *                                multiplies on operands with holes), 1 (32x32-bit ones)
+ *   GF2X_KNOB_CVT_TAYLOR         the Taylor part of BasisCvt / iBasisCvt at lengths
+ *                                2^25 .. 2^32 inside a product: 1 (two superset-sum
+ *                                passes over HBM, the default), 0 (one pass per division
+ *                                step of Alg. 1 above the Taylor window kernel)
  * GF2X_EINVAL for a NULL context, an unknown knob or choice < -1.  Not
  * thread-safe against calls running on the same context. */
 enum {
@@ -280,7 +284,8 @@ enum {
     GF2X_KNOB_BOTTOM_DEPTH = 5,
     GF2X_KNOB_M128_BOTTOM_DEPTH = 6,
     GF2X_KNOB_BATCH_PERSISTENT = 7,
-    GF2X_KNOB_BOTTOM_MUL = 8
+    GF2X_KNOB_BOTTOM_MUL = 8,
+    GF2X_KNOB_CVT_TAYLOR = 9
 };
 GF2X_API gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice);
 

@@ -21,7 +21,8 @@ from .build import LIB as LIB_PATH, LIB_DEBUG as LIB_DEBUG_PATH
 __all__ = ["Context", "Gf2xError", "PreparedBatch", "load_library", "transform_bits", "workspace_bytes",
            "host_workspace_bytes", "product_bits", "m128_transform_bits", "m128_workspace_bytes",
            "ABI_FUNCTIONS", "STATUS", "KNOB_UNIT16_R", "KNOB_BOTTOM_SHAPE", "KNOB_WINDOW_DEPTH",
-           "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH", "KNOB_BATCH_PERSISTENT", "KNOB_BOTTOM_MUL"]
+           "KNOB_M128_BOTTOM_CHUNK", "KNOB_BOTTOM_DEPTH", "KNOB_M128_BOTTOM_DEPTH", "KNOB_BATCH_PERSISTENT", "KNOB_BOTTOM_MUL",
+           "KNOB_CVT_TAYLOR"]
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ETOOBIG", 3: "GF2X_ENOMEM", 4: "GF2X_ECUDA",
           5: "GF2X_ETIMEOUT", 6: "GF2X_ENODEV", 7: "GF2X_ENOSPACE", 8: "GF2X_EBOUNDS"}
@@ -91,6 +92,7 @@ KNOB_BOTTOM_DEPTH = 5          # 8 .. 11
 KNOB_M128_BOTTOM_DEPTH = 6     # 8 .. 10
 KNOB_BATCH_PERSISTENT = 7      # 1 (one persistent launch per batch), 0 (launches per kernel and size class)
 KNOB_BOTTOM_MUL = 8            # 0 (16-bit integer product form), 1 (32-bit form) in the fused bottom kernel
+KNOB_CVT_TAYLOR = 9            # BasisCvt's Taylor part at 2^25..2^32 bits: 1 (two superset-sum passes), 0 (division steps)
 
 
 class Job(ctypes.Structure):

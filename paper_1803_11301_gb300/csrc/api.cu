@@ -318,6 +318,9 @@ struct ClassRun {
     u64 stride;                     // words between the buffers of consecutive jobs
 };
 
+// Words of one job's X, Y or T buffer.
+u64 buffer_words(const ClassRun &r) { return r.count == 1 && r.stride == 0 ? buffer_bytes(r.n) / 8 : r.stride; }
+
 // Lines 1-2 (or 4-5) of Alg. 5 for one operand of every job: load, BasisCvt, Encode.
 gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStream_t st)
 {
@@ -328,8 +331,16 @@ gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStr
         if (r.jobs) TRY(gf2x::load_jobs(ctx, r.jobs, which, r.T, r.stride, r.n / 64, r.count, st));
         else TRY(gf2x::load_bits(ctx, which ? r.b : r.a, which ? r.nb : r.na, r.T, r.n / 64, st));
     }
-    // F (the Encode output, free until then) is the scratch buffer of BasisCvt
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st)); }
+    // F (the Encode output, free until then) is the scratch buffer of BasisCvt;
+    // its side buffer is Y for a (free until b's forward steps) and, for b, the
+    // words of T above L (Encode reads only the first L bits)
+    const u64 words = buffer_words(r);
+    u64 *side = which ? r.T + L / 64 : r.Y;
+    const u64 side_words = which ? words - L / 64 : words;
+    {
+        StageScope s(ctx, STAGE_BASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st, side, r.stride, side_words));
+    }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, r.stride, st)); }
     return GF2X_OK;
 }
@@ -346,7 +357,10 @@ gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
         StageScope s(ctx, STAGE_LOAD, st);
         TRY(gf2x::load_pair(ctx, r.a, r.na, r.b, r.nb, r.T, half, half, st));
     }
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.La, false, 2, half, r.X, st)); }
+    {   // Y (free until Encode) is the side buffer, laid out like X
+        StageScope s(ctx, STAGE_BASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, r.T, r.La, false, 2, half, r.X, st, r.Y, half, half));
+    }
     {
         StageScope s(ctx, STAGE_ENCODE, st);
         TRY(gf2x::encode(ctx, r.T, l, r.X, r.La, 2, half, (u64)(r.Y - r.X), st));
@@ -363,8 +377,12 @@ gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st, int 
     const u64 sd = r.stride;
     { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::butterfly_top_inverse(ctx, r.X, l, cnt, sd, st, bt)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, r.X, l, r.T, cnt, sd, st)); }
-    // X is free once Decode has read it: the scratch buffer of iBasisCvt
-    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st)); }
+    // X is free once Decode has read it: the scratch buffer of iBasisCvt; Y
+    // (free after the pointwise product) its side buffer
+    {
+        StageScope g(ctx, STAGE_IBASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st, r.Y, sd, buffer_words(r)));
+    }
     {
         StageScope g(ctx, STAGE_STORE, st);
         if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
@@ -425,9 +443,9 @@ gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n,
     const int l = log2_u64(n) - 6;
     const u64 L = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
     const size_t buf = buffer_bytes(n);
-    u64 *X = (u64 *)ws, *T = (u64 *)((char *)ws + 2 * buf);
+    u64 *X = (u64 *)ws, *Y = (u64 *)((char *)ws + buf), *T = (u64 *)((char *)ws + 2 * buf);
     { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, b, nb, T, n / 64, st)); }
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st)); }
+    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st, Y, 0, buf / 8)); }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, bhat, L, 1, 0, 0, st)); }
     { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, bhat, l, false, 1, 0, st, T)); }
     return GF2X_OK;
@@ -445,6 +463,7 @@ gf2x_status mul_transformed_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u6
     r.a = a; r.na = na; r.nb = nb; r.c = c;
     const size_t buf = buffer_bytes(r.n);
     r.X = (u64 *)ws;
+    r.Y = (u64 *)((char *)ws + buf);        // free: b's transform is bhat
     r.T = (u64 *)((char *)ws + 2 * buf);
     const int l = log2_u64(r.n) - 6;
     gf2x_status s = forward(ctx, r, 0, r.X, st);
@@ -960,12 +979,12 @@ static_assert(GF2X_KNOB_UNIT16_R == gf2x::TUNE_UNIT16_R && GF2X_KNOB_BOTTOM_SHAP
                   GF2X_KNOB_BOTTOM_DEPTH == gf2x::TUNE_BFLY_DEPTH &&
                   GF2X_KNOB_M128_BOTTOM_DEPTH == gf2x::TUNE_M128_BFLY_DEPTH &&
                   GF2X_KNOB_BATCH_PERSISTENT == gf2x::TUNE_BATCH_PERSIST &&
-                  GF2X_KNOB_BOTTOM_MUL == gf2x::TUNE_BOTTOM_MUL,
+                  GF2X_KNOB_BOTTOM_MUL == gf2x::TUNE_BOTTOM_MUL && GF2X_KNOB_CVT_TAYLOR == gf2x::TUNE_CVT_TAYLOR,
               "the ABI's knob numbers are the tuner's");
 
 gf2x_status gf2x_tune_pin(gf2x_ctx *ctx, int knob, int choice)
 {
-    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_BOTTOM_MUL || choice < -1) return GF2X_EINVAL;
+    if (!ctx || knob < GF2X_KNOB_UNIT16_R || knob > GF2X_KNOB_CVT_TAYLOR || choice < -1) return GF2X_EINVAL;
     gf2x::tuner_pin(ctx->tuner, knob, choice);
     ++graphs(ctx)->gen;           // captured graphs keep their shapes: capture again
     return GF2X_OK;
@@ -1103,7 +1122,7 @@ gf2x_status gf2x_stream_status(gf2x_ctx *ctx, void *stream)
     }
     const unsigned long long oob = gf2x::out_of_range_fft() + gf2x::out_of_range_cvt() +
                                    gf2x::out_of_range_cvt_reg() + gf2x::out_of_range_bfly() +
-                                   gf2x::out_of_range_persist();
+                                   gf2x::out_of_range_persist() + gf2x::out_of_range_zeta();
     if (h == 0 && oob) return GF2X_EBOUNDS;
     return (gf2x_status)h;
 }

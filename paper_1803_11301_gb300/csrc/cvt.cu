@@ -302,10 +302,45 @@ cudaError_t taylor_window_launch(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L
 // `bits`), and the part next to it moves the data back: forward, window
 // bits -> scratch and (b) scratch -> bits; inverse, (b) bits -> scratch and
 // the window scratch -> bits.
+//
+// With a side buffer and m >= 9 (where (a) needs wide steps), (a) is instead
+// the two superset-sum passes of cvt_zeta.cu (bits -> scratch and side ->
+// bits) and (b) runs in place on bits.
 cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, int K, bool inverse, int count,
-                                 u64 stride, cudaStream_t st)
+                                 u64 stride, cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0,
+                                 u64 side_words = 0)
 {
     const int m = K - 16;
+    const u64 need = taylor_zeta_side_words(m);
+    if (side && need && need <= side_words && !recording(ctx)) {
+        static const int cands[2] = {0, 1};
+        if (tune_pinned(ctx, TUNE_CVT_TAYLOR, cands, 2, 1) == 1) {
+            std::vector<Step> outer_taylor;
+            if (m >= 10)
+                for (int k = m - 9; k >= 0; --k) outer_taylor.push_back({1ull << (24 + k), 1ull << (16 + k)});
+            const std::vector<Step> outer_taylor_inv(outer_taylor.rbegin(), outer_taylor.rend());
+            if (!inverse) {
+                TRY_CUDA(taylor_zeta(ctx, bits, scratch, side, side_stride, m, false, count, stride, st));
+                if (m <= 9) {
+                    TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m, kUnitWordsLog, false, count, stride, st));
+                } else {
+                    TRY_CUDA(run_steps_generic(ctx, bits, bits, L, outer_taylor, false, count, stride, st));
+                    TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, false, count, stride, st));
+                    TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, 8, kUnitWordsLog, false, count, stride, st));
+                }
+                return basis_cvt_unit16(ctx, bits, L, false, count, stride, scratch, st);
+            }
+            TRY_CUDA(basis_cvt_unit16(ctx, bits, L, true, count, stride, scratch, st));
+            if (m <= 9) {
+                TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m, kUnitWordsLog, true, count, stride, st));
+            } else {
+                TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, 8, kUnitWordsLog, true, count, stride, st));
+                TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, true, count, stride, st));
+                TRY_CUDA(run_steps_generic(ctx, bits, bits, L, outer_taylor_inv, true, count, stride, st));
+            }
+            return taylor_zeta(ctx, bits, scratch, side, side_stride, m, true, count, stride, st);
+        }
+    }
     // Layers in the window kernel (at most 8; the rest are wide steps): its
     // cost grows faster than linearly with the depth (the halo and the rows
     // per block double with each layer), so deep windows pay most while the
@@ -359,11 +394,12 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
 }  // namespace
 
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
-                      cudaStream_t st)
+                      cudaStream_t st, u64 *side, u64 side_stride, u64 side_words)
 {
     int K = 0;
     while ((1ull << K) < L) ++K;
-    if (scratch && K >= 18 && K <= 32) return basis_cvt_structured(ctx, bits, scratch, L, K, inverse, count, stride, st);
+    if (scratch && K >= 18 && K <= 32)
+        return basis_cvt_structured(ctx, bits, scratch, L, K, inverse, count, stride, st, side, side_stride, side_words);
     std::vector<Step> steps;
     build_steps(K, 1, steps);
     if (scratch && K > 32) {

@@ -365,7 +365,7 @@ namespace gf2x {
 // The same numbers as the GF2X_KNOB_* constants of the C ABI.
 enum TuneKnob {
     TUNE_UNIT16_R = 1, TUNE_BOTTOM_SHAPE = 2, TUNE_WINDOW_DEPTH = 3, TUNE_M128_BOTTOM_CHUNK = 4, TUNE_BFLY_DEPTH = 5,
-    TUNE_M128_BFLY_DEPTH = 6, TUNE_BATCH_PERSIST = 7, TUNE_BOTTOM_MUL = 8, TUNE_KNOB_END = 9
+    TUNE_M128_BFLY_DEPTH = 6, TUNE_BATCH_PERSIST = 7, TUNE_BOTTOM_MUL = 8, TUNE_CVT_TAYLOR = 9, TUNE_KNOB_END = 10
 };
 void *tuner_create();
 void tuner_destroy(void *t);
@@ -396,8 +396,18 @@ int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback);
 // BasisCvt (or iBasisCvt) in place on bits.  `scratch`, if not null, is a
 // buffer laid out like `bits` (count x stride words) whose contents may be
 // overwritten; with it, 2^18 <= L <= 2^32 run the structured kernels.
+// `side`, if not null, is a second free buffer of `side_words` words per job,
+// `side_stride` apart: with it (and taylor_zeta_side_words(K - 16) <=
+// side_words), 2^25 <= L <= 2^32 run the Taylor part as two superset-sum passes.
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
-                      cudaStream_t st);
+                      cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0, u64 side_words = 0);
+// Side-buffer words per job the two-pass Taylor part needs for 2^m rows of
+// 2^16 bits (9 <= m <= 16), else 0.
+u64 taylor_zeta_side_words(int m);
+// The Taylor part of BasisCvt / iBasisCvt of length 2^(m + 16) in two passes
+// (bits -> scratch and side -> bits); cvt_zeta.cu.
+cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 side_stride, int m, bool inverse,
+                        int count, u64 stride, cudaStream_t st);
 // BasisCvt inside every 2^16-bit block of an L-bit array (L a multiple of 2^16).
 // scratch (nullable): a free buffer laid out like bits, for the tuner.
 cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
@@ -470,6 +480,7 @@ unsigned long long out_of_range_cvt();
 unsigned long long out_of_range_cvt_reg();
 unsigned long long out_of_range_bfly();
 unsigned long long out_of_range_persist();
+unsigned long long out_of_range_zeta();
 
 // gf2x_mul (same arguments and checks) with every kernel launched directly,
 // never through the CUDA graph cache (api.cu).

@@ -68,14 +68,14 @@ def test_null_context_rejected(lib):
 def test_knob_constants_match_the_header():
     import re
     from paper_1803_11301_gb300 import (KNOB_BATCH_PERSISTENT, KNOB_BOTTOM_DEPTH, KNOB_BOTTOM_MUL, KNOB_BOTTOM_SHAPE,
-                                        KNOB_M128_BOTTOM_CHUNK, KNOB_M128_BOTTOM_DEPTH, KNOB_UNIT16_R,
+                                        KNOB_CVT_TAYLOR, KNOB_M128_BOTTOM_CHUNK, KNOB_M128_BOTTOM_DEPTH, KNOB_UNIT16_R,
                                         KNOB_WINDOW_DEPTH)
     text = open(HEADER).read()
     want = {k: int(v) for k, v in re.findall(r"GF2X_KNOB_(\w+) = (\d+)", text)}
     assert want == {"UNIT16_R": KNOB_UNIT16_R, "BOTTOM_SHAPE": KNOB_BOTTOM_SHAPE, "WINDOW_DEPTH": KNOB_WINDOW_DEPTH,
                     "M128_BOTTOM_CHUNK": KNOB_M128_BOTTOM_CHUNK, "BOTTOM_DEPTH": KNOB_BOTTOM_DEPTH,
                     "M128_BOTTOM_DEPTH": KNOB_M128_BOTTOM_DEPTH, "BATCH_PERSISTENT": KNOB_BATCH_PERSISTENT,
-                    "BOTTOM_MUL": KNOB_BOTTOM_MUL}
+                    "BOTTOM_MUL": KNOB_BOTTOM_MUL, "CVT_TAYLOR": KNOB_CVT_TAYLOR}
 
 
 def test_no_device_path_reports_enodev(lib):

@@ -59,7 +59,7 @@ def test_pin_arguments(ctx):
     with pytest.raises(Gf2xError):
         ctx.tune_pin(0, 9)
     with pytest.raises(Gf2xError):
-        ctx.tune_pin(9, 9)
+        ctx.tune_pin(10, 9)
     with pytest.raises(Gf2xError):
         ctx.tune_pin(5, -2)
     ctx.tune_pin(5, -1)                                   # releasing an unpinned knob is fine
