@@ -270,10 +270,11 @@ GF2X_API gf2x_status gf2x_tune_freeze(gf2x_ctx *ctx, int frozen);
  *   GF2X_KNOB_BOTTOM_MUL         the GF(2^64) products of the fused bottom kernel's
  *                                integer layers and pointwise step: 0 (16x16-bit integer
  *                                multiplies on operands with holes), 1 (32x32-bit ones)
- *   GF2X_KNOB_CVT_TAYLOR         the Taylor part of BasisCvt / iBasisCvt at lengths
- *                                2^25 .. 2^32 inside a product: 1 (two superset-sum
- *                                passes over HBM, the default), 0 (one pass per division
- *                                step of Alg. 1 above the Taylor window kernel)
+ *   GF2X_KNOB_CVT_TAYLOR         the Taylor parts of BasisCvt / iBasisCvt at lengths
+ *                                2^25 .. 2^32 inside a product (at 2^16-bit rows and, from
+ *                                2^26 on, at 2^24-bit blocks of the outer conversion):
+ *                                1 (superset-sum passes over HBM, the default), 0 (the
+ *                                division steps of Alg. 1, one or two per pass)
  * GF2X_EINVAL for a NULL context, an unknown knob or choice < -1.  Not
  * thread-safe against calls running on the same context. */
 enum {

@@ -305,7 +305,8 @@ cudaError_t taylor_window_launch(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L
 //
 // With a side buffer and m >= 9 (where (a) needs wide steps), (a) is instead
 // the two superset-sum passes of cvt_zeta.cu (bits -> scratch and side ->
-// bits) and (b) runs in place on bits.
+// bits), (b) runs in place on bits, and for m >= 10 the Taylor steps of (b)
+// are the row-level superset sum and carry passes of cvt_zeta.cu.
 cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, int K, bool inverse, int count,
                                  u64 stride, cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0,
                                  u64 side_words = 0)
@@ -315,16 +316,12 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
     if (side && need && need <= side_words && !recording(ctx)) {
         static const int cands[2] = {0, 1};
         if (tune_pinned(ctx, TUNE_CVT_TAYLOR, cands, 2, 1) == 1) {
-            std::vector<Step> outer_taylor;
-            if (m >= 10)
-                for (int k = m - 9; k >= 0; --k) outer_taylor.push_back({1ull << (24 + k), 1ull << (16 + k)});
-            const std::vector<Step> outer_taylor_inv(outer_taylor.rbegin(), outer_taylor.rend());
             if (!inverse) {
                 TRY_CUDA(taylor_zeta(ctx, bits, scratch, side, side_stride, m, false, count, stride, st));
                 if (m <= 9) {
                     TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m, kUnitWordsLog, false, count, stride, st));
                 } else {
-                    TRY_CUDA(run_steps_generic(ctx, bits, bits, L, outer_taylor, false, count, stride, st));
+                    TRY_CUDA(outer_taylor_zeta(ctx, bits, side, side_stride, m, false, count, stride, st));
                     TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, false, count, stride, st));
                     TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, 8, kUnitWordsLog, false, count, stride, st));
                 }
@@ -336,7 +333,7 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
             } else {
                 TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, 8, kUnitWordsLog, true, count, stride, st));
                 TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, true, count, stride, st));
-                TRY_CUDA(run_steps_generic(ctx, bits, bits, L, outer_taylor_inv, true, count, stride, st));
+                TRY_CUDA(outer_taylor_zeta(ctx, bits, side, side_stride, m, true, count, stride, st));
             }
             return taylor_zeta(ctx, bits, scratch, side, side_stride, m, true, count, stride, st);
         }

@@ -30,7 +30,8 @@
 //
 // Pass 2 (k_cvt_zeta_lo) takes the row bits 0..5: 64 consecutive rows, shifts
 // below one word.  A block skews each row u of its group by u bits (33 skewed
-// words from 34 loaded), XORs, unskews 32 output words, and for output words
+// words from 34 loaded), XORs, unskews 32 output words (one thread per skewed
+// word and octet of rows), and for output words
 // below J adds the carries, from the rows' overflow words computed the same
 // way in a second window.  The carry into the group's first row comes from the
 // last row of the previous group: all its low row bits are set, so its
@@ -45,7 +46,7 @@ constexpr int kRowWords = 1024;          // tau = 2^16 bits
 constexpr int kZetaThreads = 256;
 constexpr int kLoW = 32;                 // pass 2: output words per block and row
 constexpr int kLoLoad = kLoW + 3;        // widest loaded window (the overflow one)
-constexpr int kLoSkew = kLoW + 2;
+constexpr int kLoThreads = (8 * (kLoW + 2) + 31) / 32 * 32;   // a task per (skewed word, row octet) of the widest window
 
 // 8-byte copy global -> shared, or zeros when `valid` is false (no bytes read).
 __device__ __forceinline__ void copy8_or_zero(u64 *dst_shared, const u64 *src, bool valid)
@@ -138,65 +139,96 @@ __device__ __forceinline__ const u64 *p_word(const u64 *main, const u64 *side, u
     return xs < J - 1 - (int)(row >> 6) ? side + row * J + xs : nullptr;
 }
 
-// Pass 2 window: gt of the 64 rows row0 .. row0+63 for the words
-// [x0, x0 + nsk - 1), from P's words [x0 - 1, x0 + nsk); into out[u * ostride + o].
-__device__ __forceinline__ void lo_window(const u64 *main, const u64 *side, unsigned row0, int x0, int nsk, int J,
-                                          unsigned rows, u64 *tile, u64 *S, u64 *out, int ostride)
+// Bits [64 - s, 128 - s) of the 128-bit (hi:lo), i.e. (hi << s) | (lo >> (64 - s)),
+// for 0 <= s < 64 (s = 0: hi), in 32-bit funnel shifts.
+__device__ __forceinline__ u64 shl_pair(u64 hi, u64 lo, unsigned s)
 {
-    const int nld = nsk + 1;
-    for (int e = (int)threadIdx.x; e < 64 * nld; e += kZetaThreads) {
-        const int u = e / nld, k = e - u * nld;
+    unsigned h0 = (unsigned)hi, h1 = (unsigned)(hi >> 32), l1 = (unsigned)(lo >> 32);
+    if (s & 32) {
+        h1 = h0;
+        h0 = l1;
+        l1 = (unsigned)lo;
+    }
+    const unsigned r = s & 31;
+    return ((u64)__funnelshift_l(h0, h1, r) << 32) | __funnelshift_l(l1, h0, r);
+}
+
+// Bits [s, s + 64) of the 128-bit (hi:lo), i.e. (lo >> s) | (hi << (64 - s)),
+// for 0 <= s < 64 (s = 0: lo).
+__device__ __forceinline__ u64 shr_pair(u64 hi, u64 lo, unsigned s)
+{
+    unsigned l0 = (unsigned)lo, l1 = (unsigned)(lo >> 32), h0 = (unsigned)hi;
+    if (s & 32) {
+        l0 = l1;
+        l1 = h0;
+        h0 = (unsigned)(hi >> 32);
+    }
+    const unsigned r = s & 31;
+    return ((u64)__funnelshift_r(l1, h0, r) << 32) | __funnelshift_r(l0, l1, r);
+}
+
+// Pass 2 window, first part: P's words [x0 - 1, x0 + NSK) of the 64 rows
+// row0 .. row0+63 into buf (row pitch NSK + 1), each row u skewed by u bits
+// and summed over the row bits 0..5, in place: afterwards buf[u (NSK + 1) + s]
+// holds word x0 + s of x^u gt_u, s < NSK.  One task per (skewed word, row
+// octet): NSK x 8 <= kLoThreads.
+template <int NSK>
+__device__ __forceinline__ void lo_window_sum(const u64 *main, const u64 *side, unsigned row0, int x0, int J,
+                                              unsigned rows, u64 *buf)
+{
+    constexpr int NLD = NSK + 1;
+    static_assert(8 * NSK <= kLoThreads, "one task per thread");
+    for (int e = (int)threadIdx.x; e < 64 * NLD; e += kLoThreads) {
+        const int u = e / NLD, k = e - u * NLD;
         const u64 *p = p_word(main, side, row0 + u, x0 - 1 + k, J, rows);
-        copy8_or_zero(tile + e, p ? p : main, p != nullptr);
+        copy8_or_zero(buf + e, p ? p : main, p != nullptr);
     }
     cvtk::copy_async_wait();
     __syncthreads();
-    // skew row u by u bits, then the layers of row bits 0..2 in registers
-    for (int task = (int)threadIdx.x; task < nsk * 8; task += kZetaThreads) {
-        const int sg = task % nsk, a = task / nsk;
-        u64 v[8];
+    const int task = (int)threadIdx.x;
+    const bool active = task < NSK * 8;
+    const int sg = task % NSK, a = task / NSK;
+    u64 v[8];
+    if (active) {                                   // skew, then row bits 0..2 in registers
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int u = 8 * a + i;
-            const u64 hi = tile[u * nld + sg + 1], lo = tile[u * nld + sg];
-            v[i] = u == 0 ? hi : (hi << u) | (lo >> (64 - u));
+            v[i] = shl_pair(buf[u * NLD + sg + 1], buf[u * NLD + sg], (unsigned)u);
         }
         superset_sum<3>(v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) S[(8 * a + i) * nsk + sg] = v[i];
     }
-    __syncthreads();
-    for (int task = (int)threadIdx.x; task < nsk * 8; task += kZetaThreads) {   // row bits 3..5
-        const int sg = task % nsk, b = task / nsk;
-        u64 v[8];
+    __syncthreads();                                // every read of the loaded words is done
+    if (active)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = S[(b + 8 * i) * nsk + sg];
+        for (int i = 0; i < 8; ++i) buf[(8 * a + i) * NLD + sg] = v[i];
+    __syncthreads();
+    if (active) {                                   // row bits 3..5 (a is now the row's low octet index)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = buf[(a + 8 * i) * NLD + sg];
         superset_sum<3>(v);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) S[(b + 8 * i) * nsk + sg] = v[i];
+        for (int i = 0; i < 8; ++i) buf[(a + 8 * i) * NLD + sg] = v[i];
     }
     __syncthreads();
-    for (int e = (int)threadIdx.x; e < 64 * (nsk - 1); e += kZetaThreads) {    // unskew
-        const int u = e / (nsk - 1), o = e - u * (nsk - 1);
-        const u64 lo = S[u * nsk + o], hi = S[u * nsk + o + 1];
-        out[u * ostride + o] = u == 0 ? lo : (lo >> u) | (hi << (64 - u));
-    }
-    __syncthreads();
+}
+
+// Word o of gt_u from the summed window (pitch nld): unskew by u bits.
+__device__ __forceinline__ u64 lo_unskew(const u64 *buf, int nld, int u, int o)
+{
+    return shr_pair(buf[u * nld + o + 1], buf[u * nld + o], (unsigned)u);
 }
 
 // Pass 2: row bits 0..5 and the carries.  Block (group of 64 rows, window c of
 // 32 output words); main (+ side) -> dst.
 template <bool INV>
-__global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_lo(const u64 *__restrict__ main, const u64 *__restrict__ side,
-                                                               u64 *__restrict__ dst, u64 stride, u64 side_stride, int J,
-                                                               unsigned rows)
+__global__ void __launch_bounds__(kLoThreads) k_cvt_zeta_lo(const u64 *__restrict__ main, const u64 *__restrict__ side,
+                                                             u64 *__restrict__ dst, u64 stride, u64 side_stride, int J,
+                                                             unsigned rows)
 {
     extern __shared__ u64 zs[];
-    u64 *tile = zs;                                   // 64 x kLoLoad
-    u64 *S = tile + 64 * kLoLoad;                     // 64 x kLoSkew
-    u64 *O = S + 64 * kLoSkew;                        // 64 x (kLoW + 1): overflow words [c - 1, c + kLoW)
-    u64 *G = O + 64 * (kLoW + 1);                     // 64 x kLoW: gt of the output words
-    u64 *prev = G + 64 * kLoW;                        // kLoW: overflow of the previous group's last row
+    u64 *buf = zs;                                    // 64 x kLoLoad: loaded, then summed words
+    u64 *O = buf + 64 * kLoLoad;                      // 64 x (kLoW + 1): overflow words [c - 1, c + kLoW)
+    u64 *prev = O + 64 * (kLoW + 1);                  // kLoW: overflow of the previous group's last row
     constexpr int nwin = kRowWords / kLoW;
     const unsigned grp = blockIdx.x / nwin;
     const int c = (int)(blockIdx.x % nwin) * kLoW;
@@ -210,12 +242,17 @@ __global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_lo(const u64 *__restr
             const u64 *p = grp > 0 ? p_word(main, side, row0 - 1, kRowWords + c + (int)threadIdx.x, J, rows) : nullptr;
             prev[threadIdx.x] = p ? *p : 0;
         }
-        lo_window(main, side, row0, kRowWords + c - 1, kLoW + 2, J, rows, tile, S, O, kLoW + 1);
+        lo_window_sum<kLoW + 2>(main, side, row0, kRowWords + c - 1, J, rows, buf);
+        for (int e = (int)threadIdx.x; e < 64 * (kLoW + 1); e += kLoThreads) {
+            const int u = e / (kLoW + 1), o = e - u * (kLoW + 1);
+            O[e] = lo_unskew(buf, kLoW + 3, u, o);
+        }
+        __syncthreads();
     }
-    lo_window(main, side, row0, c, kLoW + 1, J, rows, tile, S, G, kLoW);
-    for (int e = (int)threadIdx.x; e < 64 * kLoW; e += kZetaThreads) {
+    lo_window_sum<kLoW + 1>(main, side, row0, c, J, rows, buf);
+    for (int e = (int)threadIdx.x; e < 64 * kLoW; e += kLoThreads) {
         const int u = e / kLoW, o = e - u * kLoW, v = c + o;
-        u64 val = G[u * kLoW + o];
+        u64 val = lo_unskew(buf, kLoW + 2, u, o);
         if (carry) {
             const u64 op = u ? O[(u - 1) * (kLoW + 1) + o + 1] : prev[o];
             if (!INV) {
@@ -230,7 +267,7 @@ __global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_lo(const u64 *__restr
     }
 }
 
-constexpr size_t kLoSmem = (size_t)(64 * (kLoLoad + kLoSkew + (kLoW + 1) + kLoW) + kLoW) * 8;
+constexpr size_t kLoSmem = (size_t)(64 * (kLoLoad + (kLoW + 1)) + kLoW) * 8;
 
 template <int NB>
 cudaError_t zeta_hi_launch(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st)
@@ -247,6 +284,118 @@ cudaError_t zeta_hi_launch(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 
         configured = true;
     }
     k_cvt_zeta_hi<NB><<<dim3(64 * NWIN, (unsigned)count), kZetaThreads, smem, st>>>(src, dst, side, stride, side_stride);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ outer Taylor part
+// The outer conversion of Alg. 1 (on the 2^m rows of 2^16 bits as units)
+// starts with its own Taylor expansion at z^256 + z, z = x^tau: steps
+// (256 2^k, 2^k) rows, k = m-9 .. 0.  A shift by whole rows moves every word
+// column on its own, so the same reformulation holds per column with rows in
+// place of bits: for the blocks F_Q of 256 rows (B = 2^(m-8) of them),
+//     gt_R = sum_{Q superset of R} z^(Q - R) F_Q     (up to B - 1 - R rows beyond the block),
+//     G_R = (gt_R mod z^256) + z o_R + o_{R-1}       (forward; o_R the overflow rows),
+//     F_Q = (ft_Q mod z^256) + o_{Q-1}                (inverse, ft the same sum).
+// Pass A (k_cvt_unit_zeta): a block holds, for one skewed row position
+// p' = p + Q, a slab of W word columns of every block Q (row Q 256 + p' - Q),
+// sums over the NQ = m - 8 block bits and writes row R 256 + p' - R back (in
+// place: the same rows it read) or overflow row p' - R - 256 of block R to the
+// side buffer (B rows of 1024 words per block).  Pass B (k_cvt_unit_fix) adds
+// the overflow rows to the first B rows of every block.
+template <int NQ>
+struct UnitShape {
+    static constexpr int A = NQ < 4 ? NQ : 4;     // block bits in registers, first phase
+    static constexpr int B = NQ - A;              // second phase, through shared memory
+    static constexpr int NB = 1 << NQ;            // blocks
+    static constexpr int W = kZetaThreads >> B;   // word columns per CTA
+    static constexpr size_t SMEM = B > 0 ? (size_t)NB * W * 8 : 0;
+};
+
+template <int NQ>
+__global__ void __launch_bounds__(kZetaThreads) k_cvt_unit_zeta(u64 *__restrict__ bits, u64 *__restrict__ side,
+                                                                 u64 stride, u64 side_stride)
+{
+    using Sh = UnitShape<NQ>;
+    constexpr int A = Sh::A, B = Sh::B, NB = Sh::NB, W = Sh::W;
+    constexpr int NCB = kRowWords / W;
+    extern __shared__ u64 ut[];                       // [NB][W] between the phases
+    const int pp = (int)(blockIdx.x / NCB);           // skewed row position, 0 .. 256 + NB - 2
+    const int c0 = (int)(blockIdx.x % NCB) * W;
+    bits += (u64)blockIdx.y * stride;
+    side += (u64)blockIdx.y * side_stride;
+    constexpr u64 kWords = (u64)kRowWords << (NQ + 8);
+    auto store = [&](int r, int w, u64 val) {
+        const int p = pp - r;                         // row of block r
+        if (p < 0) return;
+        if (p < 256) {
+            const unsigned i = (unsigned)(r * 256 + p) * kRowWords + c0 + w;
+            if (in_range(i, kWords)) bits[i] = val;
+        } else if (p - 256 < NB - 1 - r) {
+            const unsigned i = (unsigned)(r * NB + p - 256) * kRowWords + c0 + w;
+            if (in_range(i, (u64)NB * NB * kRowWords)) side[i] = val;
+        }
+    };
+    const int w = (int)threadIdx.x % W, s = (int)threadIdx.x / W;
+    u64 v[1 << A];
+#pragma unroll
+    for (int i = 0; i < (1 << A); ++i) {
+        const int q = (s << A) + i, p = pp - q;
+        const unsigned idx = (unsigned)(q * 256 + p) * kRowWords + c0 + w;
+        v[i] = (p >= 0 && p < 256 && in_range(idx, kWords)) ? bits[idx] : 0;
+    }
+    superset_sum<A>(v);
+    if constexpr (B == 0) {
+#pragma unroll
+        for (int i = 0; i < (1 << A); ++i) store((s << A) + i, w, v[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < (1 << A); ++i) ut[((s << A) + i) * W + w] = v[i];
+        __syncthreads();
+        for (int task = (int)threadIdx.x; task < (W << A); task += kZetaThreads) {
+            const int ww = task % W, b = task / W;
+            u64 x[1 << B];
+#pragma unroll
+            for (int i = 0; i < (1 << B); ++i) x[i] = ut[(b + (i << A)) * W + ww];
+            superset_sum<B>(x);
+#pragma unroll
+            for (int i = 0; i < (1 << B); ++i) store(b + (i << A), ww, x[i]);
+        }
+    }
+}
+
+// Pass B: rows p < B of block r get o_{r-1}[p] and (forward) o_r[p - 1].
+template <bool INV>
+__global__ void __launch_bounds__(kZetaThreads) k_cvt_unit_fix(u64 *__restrict__ bits, const u64 *__restrict__ side,
+                                                                int NB, u64 stride, u64 side_stride)
+{
+    bits += (u64)blockIdx.y * stride;
+    side += (u64)blockIdx.y * side_stride;
+    const u64 e = (u64)blockIdx.x * kZetaThreads + threadIdx.x;   // (block r, row p < NB, word c)
+    const int c = (int)(e % kRowWords);
+    const u64 rp = e / kRowWords;
+    const int p = (int)(rp % (u64)NB), r = (int)(rp / (u64)NB);
+    if (r >= NB) return;
+    auto o = [&](int rr, int t) -> u64 {               // overflow row t of block rr, zero beyond its degree
+        return rr >= 0 && t >= 0 && t < NB - 1 - rr ? side[((u64)rr * NB + t) * kRowWords + c] : 0;
+    };
+    u64 add = o(r - 1, p);
+    if (!INV) add ^= o(r, p - 1);
+    const u64 i = ((u64)r * 256 + p) * kRowWords + c;
+    if (in_range(i, (u64)NB * 256 * kRowWords)) bits[i] ^= add;
+}
+
+template <int NQ>
+cudaError_t unit_zeta_launch(u64 *bits, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st)
+{
+    using Sh = UnitShape<NQ>;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_cvt_unit_zeta<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(Sh::SMEM ? Sh::SMEM : 1));
+        configured = true;
+    }
+    const unsigned grid = (unsigned)((256 + Sh::NB - 1) * (kRowWords / Sh::W));
+    k_cvt_unit_zeta<NQ><<<dim3(grid, (unsigned)count), kZetaThreads, Sh::SMEM, st>>>(bits, side, stride, side_stride);
     return cudaGetLastError();
 }
 
@@ -285,13 +434,44 @@ cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 s
     const dim3 grid((rows / 64) * (kRowWords / kLoW), (unsigned)count);
     const int J = 1 << (m - 6);
     if (inverse)
-        k_cvt_zeta_lo<true><<<grid, kZetaThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
+        k_cvt_zeta_lo<true><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
     else
-        k_cvt_zeta_lo<false><<<grid, kZetaThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
+        k_cvt_zeta_lo<false><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
     count_launch(ctx);
     return cudaGetLastError();
 }
 
 GF2X_OUT_OF_RANGE_READER(out_of_range_zeta)
+
+}  // namespace gf2x
+
+namespace gf2x {
+
+// The Taylor part of the outer conversion of BasisCvt(2^(m + 16)) (forward)
+// or of iBasisCvt, 10 <= m <= 16: in place on bits, side as for taylor_zeta.
+cudaError_t outer_taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *side, u64 side_stride, int m, bool inverse, int count,
+                              u64 stride, cudaStream_t st)
+{
+    cudaError_t e;
+    switch (m - 8) {
+    case 2: e = unit_zeta_launch<2>(bits, side, stride, side_stride, count, st); break;
+    case 3: e = unit_zeta_launch<3>(bits, side, stride, side_stride, count, st); break;
+    case 4: e = unit_zeta_launch<4>(bits, side, stride, side_stride, count, st); break;
+    case 5: e = unit_zeta_launch<5>(bits, side, stride, side_stride, count, st); break;
+    case 6: e = unit_zeta_launch<6>(bits, side, stride, side_stride, count, st); break;
+    case 7: e = unit_zeta_launch<7>(bits, side, stride, side_stride, count, st); break;
+    case 8: e = unit_zeta_launch<8>(bits, side, stride, side_stride, count, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    count_launch(ctx);
+    const int NB = 1 << (m - 8);
+    const u64 items = (u64)NB * NB * kRowWords;
+    const dim3 grid((unsigned)((items + kZetaThreads - 1) / kZetaThreads), (unsigned)count);
+    if (inverse) k_cvt_unit_fix<true><<<grid, kZetaThreads, 0, st>>>(bits, side, NB, stride, side_stride);
+    else k_cvt_unit_fix<false><<<grid, kZetaThreads, 0, st>>>(bits, side, NB, stride, side_stride);
+    count_launch(ctx);
+    return cudaGetLastError();
+}
 
 }  // namespace gf2x

@@ -408,6 +408,10 @@ u64 taylor_zeta_side_words(int m);
 // (bits -> scratch and side -> bits); cvt_zeta.cu.
 cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 side_stride, int m, bool inverse,
                         int count, u64 stride, cudaStream_t st);
+// The Taylor part of the outer conversion (on rows of 2^16 bits) of the same
+// length, 10 <= m <= 16, in place on bits with the same side buffer.
+cudaError_t outer_taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *side, u64 side_stride, int m, bool inverse, int count,
+                              u64 stride, cudaStream_t st);
 // BasisCvt inside every 2^16-bit block of an L-bit array (L a multiple of 2^16).
 // scratch (nullable): a free buffer laid out like bits, for the tuner.
 cudaError_t basis_cvt_unit16(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
