@@ -120,6 +120,21 @@ void window_table(const u64 rows[64], u64 *tab)
         }
 }
 
+// Four-bit windows of a 64 x 64 GF(2) matrix in the layout of the Butterfly
+// kernels' multiplication tables (mul_tab): window k holds, at slot x ^ k, the
+// XOR of rows 4k + b over the bits b of x (16 windows of 16 words: one window
+// spans the 32 shared-memory banks, so lanes reading one window never conflict).
+void window_table4(const u64 rows[64], u64 *tab)
+{
+    for (int k = 0; k < 16; ++k)
+        for (int x = 0; x < 16; ++x) {
+            u64 r = 0;
+            for (int b = 0; b < 4; ++b)
+                if ((x >> b) & 1) r ^= rows[4 * k + b];
+            tab[k * 16 + (x ^ k)] = r;
+        }
+}
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -846,11 +861,12 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     }
     if (!gf2_inverse(r, rinv)) return fail(GF2X_EINVAL);   // Prop. 2
 
-    std::vector<u64> host(3 * 2048 + 64);
+    std::vector<u64> host(3 * 2048 + 64 + 256);
     window_table(v, &host[0]);
     window_table(r, &host[2048]);
     window_table(rinv, &host[4096]);
     std::memcpy(&host[6144], v, sizeof v);
+    window_table4(rinv, &host[6208]);
 
     if (cudaMalloc(&ctx->d_tables, host.size() * sizeof(u64)) != cudaSuccess) return fail(GF2X_ENOMEM);
     if (cudaMalloc(&ctx->d_state, kStateBytes) != cudaSuccess) {
@@ -864,6 +880,7 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     ctx->d_enc = ctx->d_tables + 2048;
     ctx->d_dec = ctx->d_tables + 4096;
     ctx->d_cantor = ctx->d_tables + 6144;
+    ctx->d_dec4 = ctx->d_tables + 6208;
     std::vector<u64> host128(gf2x::kTables128Words);
     if (!gf2x::m128_build_tables(host128.data())) {
         cudaFree(ctx->d_tables);

@@ -10,9 +10,8 @@ __global__ void __launch_bounds__(256) k_encode(const u64 *__restrict__ novel, u
                                                 const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups, u64 stride,
                                                 u64 out_stride)
 {
-    __shared__ __align__(16) u64 tab[8 * 256];
-    __shared__ u64 tile[64 * kPad];
-    encode_body(launch_block(), tab, tile, novel, rw, rows, enc, f, groups, stride, out_stride);
+    __shared__ __align__(2048) u64 sm[kCodecSmemWords];
+    encode_body(launch_block(), sm, novel, rw, rows, enc, f, groups, stride, out_stride);
 }
 
 __global__ void k_encode_small(const u64 *__restrict__ novel, int l, u64 nonzero_bits, const u64 *__restrict__ enc,
@@ -24,9 +23,8 @@ __global__ void k_encode_small(const u64 *__restrict__ novel, int l, u64 nonzero
 __global__ void __launch_bounds__(256) k_decode(const u64 *__restrict__ h, u64 rw, const u64 *__restrict__ dec,
                                                 u64 *__restrict__ novel, u64 groups, u64 stride)
 {
-    __shared__ __align__(16) u64 tab[8 * 256];
-    __shared__ u64 tile[64 * kPad];
-    decode_body(launch_block(), tab, tile, h, rw, dec, novel, groups, stride);
+    __shared__ __align__(128) u64 sm[kDecodeSmemWords];
+    decode_body(launch_block(), sm, h, rw, dec, novel, groups, stride);
 }
 
 __global__ void k_decode_small(const u64 *__restrict__ h, int l, const u64 *__restrict__ dec, u64 *__restrict__ novel,
@@ -158,6 +156,19 @@ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
 
+// Blocks per job of a grid-stride Encode / Decode launch: as many as are
+// resident at once over all `count` jobs (one wave), at most one per group.
+template <class Kernel>
+u64 codec_grid(gf2x_ctx *ctx, Kernel kernel, u64 groups, int count)
+{
+    static int per_sm = 0;
+    if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1))
+        per_sm = 1;
+    u64 g = (u64)per_sm * (u64)ctx->num_sms / (u64)(count > 0 ? count : 1);
+    if (g < 1) g = 1;
+    return groups < g ? groups : g;
+}
+
 cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_bits, int count, u64 stride,
                    u64 out_stride, cudaStream_t st)
 {
@@ -173,7 +184,7 @@ cudaError_t encode(gf2x_ctx *ctx, const u64 *novel, int l, u64 *f, u64 nonzero_b
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
         int rows = (int)((nonzero_bits + np - 1) / np);           // rows that can be non-zero
         if (rows > 64) rows = 64;
-        const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        const u64 grid = codec_grid(ctx, k_encode, groups, count);
         if (recording(ctx)) {
             SegRec r{SEG_ENCODE, {rows, 0, 0, 0}, (unsigned)grid, (unsigned)count, 256, kCodecSmemWords * 8,
                      (unsigned)grid, -1, {(u64)novel, rw, (u64)ctx->d_enc, (u64)f, groups, stride, out_stride}};
@@ -198,13 +209,13 @@ cudaError_t decode(gf2x_ctx *ctx, const u64 *h, int l, u64 *novel, int count, u6
     } else {
         const u64 rw = 1ull << (l - 6);
         const u64 cols = rw < kCols ? rw : kCols, groups = rw / cols;
-        const u64 grid = groups < 4 * (u64)ctx->num_sms ? groups : 4 * (u64)ctx->num_sms;
+        const u64 grid = codec_grid(ctx, k_decode, groups, count);
         if (recording(ctx)) {
-            SegRec r{SEG_DECODE, {0, 0, 0, 0}, (unsigned)grid, (unsigned)count, 256, kCodecSmemWords * 8,
-                     (unsigned)grid, -1, {(u64)h, rw, (u64)ctx->d_dec, (u64)novel, groups, stride}};
+            SegRec r{SEG_DECODE, {0, 0, 0, 0}, (unsigned)grid, (unsigned)count, 256, kDecodeSmemWords * 8,
+                     (unsigned)grid, -1, {(u64)h, rw, (u64)ctx->d_dec4, (u64)novel, groups, stride}};
             return record(ctx, r) ? cudaSuccess : cudaErrorInvalidValue;
         }
-        launch_pdl(ctx->pdl, k_decode, dim3((unsigned)grid, count), dim3(256), 0, st, h, rw, ctx->d_dec, novel, groups, stride);
+        launch_pdl(ctx->pdl, k_decode, dim3((unsigned)grid, count), dim3(256), 0, st, h, rw, ctx->d_dec4, novel, groups, stride);
     }
     count_launch(ctx);
     return cudaGetLastError();

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "gf2x_common.cuh"
+#include "gf2x_tables.cuh"
 
 // Data written by earlier work of the same launch must not be read through the
 // non-coherent read-only path: the persistent kernel defines this empty.
@@ -16,18 +17,59 @@ namespace fftk {
 
 constexpr int kCols = 32;            // word columns per Encode/Decode block
 
-// Copy a 16 KiB window table (16-byte aligned: it sits in the context's
-// cudaMalloc'd table block) to shared memory with asynchronous 16-byte copies;
-// the caller waits (cp.async.wait_all) and synchronises.
-__device__ __forceinline__ void load_table_async(const VBlock &vb, u64 *dst, const u64 *__restrict__ src)
+// R (or R^{-1}) in eight-bit windows: 8 windows of 256 words, 16 KiB.
+constexpr int kCodecTabWords = 8 * 256;
+
+// R^{-1} in four-bit windows (mul_tab layout): 16 windows of 16 words, 2 KiB.
+constexpr int kDecodeTabWords = 256;
+
+// Copy a window table of `words` words (16-byte aligned: it sits in the
+// context's cudaMalloc'd table block) to shared memory with asynchronous
+// 16-byte copies; the caller waits (cp.async.wait_all) and synchronises.
+__device__ __forceinline__ void load_table_async(const VBlock &vb, u64 *dst, const u64 *__restrict__ src, int words)
 {
-    for (int k = 2 * vb.t; k < 8 * 256; k += 2 * vb.nt)
+    for (int k = 2 * vb.t; k < words; k += 2 * vb.nt)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst + k)),
                      "l"(src + k)
                      : "memory");
 }
 
 __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// 8-byte copy global -> shared, or zeros when `valid` is false (no bytes read).
+__device__ __forceinline__ void copy8_or_zero(u64 *dst_shared, const u64 *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst_shared)),
+                 "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
+// x times the matrix whose eight-bit window table sits at shared address tab
+// (2 KiB aligned): per window, one shift and one LOP3 form the entry's address
+// (its byte offset ORed into the aligned base) and the window's 2 KiB base is
+// the load's immediate offset.  Eight lookups per point: they conflict on
+// banks, but these kernels are bound by integer instructions, of which the
+// four-bit form (16 lookups) takes twice as many.
+template <int W>
+__device__ __forceinline__ void tab8_window(u64 &r, unsigned tab, unsigned lo, unsigned hi)
+{
+    constexpr int k = 8 * (W & 3);                      // bit of byte W in its half
+    const unsigned src = W < 4 ? lo : hi;
+    const unsigned a = ((k >= 3 ? src >> (k - 3) : src << (3 - k)) & 0x7F8u) | tab;
+    u64 v;
+    asm volatile("ld.shared.u64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(W * 2048));
+    r ^= v;
+    if constexpr (W + 1 < 8) tab8_window<W + 1>(r, tab, lo, hi);
+}
+
+__device__ __forceinline__ u64 lin64_w8(unsigned tab, u64 x)
+{
+    u64 r = 0;
+    tab8_window<0>(r, tab, (unsigned)x, (unsigned)(x >> 32));
+    return r;
+}
+
+__device__ __forceinline__ u64 *align2048(u64 *p) { return (u64 *)(((uintptr_t)p + 2047) & ~(uintptr_t)2047); }
 
 // ------------------------------------------------------------------- Encode
 // n_p = 2^l >= 64.  Row j of the novelpoly bit array is bits [j n_p, (j+1) n_p),
@@ -38,30 +80,36 @@ __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_
 // A block stages 64 rows x 32 word columns in shared memory (coalesced row
 // reads); each warp transposes one column's 64x64 bit matrix with shuffles
 // (Sec. 4.4's block-swap transpose: a 32-bit half swap in registers, then
-// five exchange rounds across lanes) and applies R through 8-bit window tables
-// loaded once per block.  Rows at or above `rows` are zero and are not read.
+// five exchange rounds across lanes) and applies R through four-bit window
+// tables loaded once per block (lin64_w8).  Rows at or above `rows` are zero
+// and are not read.
 constexpr int kPad = kCols + 1;      // padded row of the staging tile
-constexpr unsigned kCodecSmemWords = 8 * 256 + 64 * kPad;   // window table + staging tile
+// window table (2 KiB aligned within the block's shared memory) + staging tile
+constexpr unsigned kCodecSmemWords = 256 + kCodecTabWords + 64 * kPad;
 
-// tab: 8 x 256 words (16-byte aligned), tile: 64 kPad words, both shared memory.
-__device__ __forceinline__ void encode_body(const VBlock &vb, u64 *tab, u64 *tile, const u64 *GF2X_DATA_RESTRICT novel,
-                                            u64 rw, int rows, const u64 *__restrict__ enc, u64 *__restrict__ f,
-                                            u64 groups, u64 stride, u64 out_stride)
+// sm: kCodecSmemWords words of shared memory (8-byte aligned).
+__device__ __forceinline__ void encode_body(const VBlock &vb, u64 *sm, const u64 *GF2X_DATA_RESTRICT novel, u64 rw,
+                                            int rows, const u64 *__restrict__ enc, u64 *__restrict__ f, u64 groups,
+                                            u64 stride, u64 out_stride)
 {
+    u64 *tab = align2048(sm), *tile = tab + kCodecTabWords;
+    const unsigned tabs = smem_addr(tab);
     novel += (u64)vb.by * stride;            // job of a batch
     f += (u64)vb.by * out_stride;
-    const int cols = rw < kCols ? (int)rw : kCols;
+    const int cols = rw < kCols ? (int)rw : kCols;   // a power of two
+    const int lc = __ffs(cols) - 1;
     const int lane = vb.t & 31, warp = vb.t >> 5;
     pdl_allow();
-    load_table_async(vb, tab, enc);                   // in flight with the first tile's loads
+    load_table_async(vb, tab, enc, kCodecTabWords);                   // in flight with the first tile's loads
     pdl_wait();
     for (u64 g = vb.bx; g < groups; g += vb.gx) {
         const u64 w0 = g * cols;
         vb.sync();
-        for (int k = vb.t; k < 64 * cols; k += vb.nt) {
-            const int j = k / cols, w = k % cols;
+        for (int k = vb.t; k < 64 * cols; k += vb.nt) {   // every load of the tile in flight at once
+            const int j = k >> lc, w = k & (cols - 1);
             const u64 src = (u64)j * rw + w0 + w;
-            tile[j * kPad + w] = (j < rows && in_range(src, 64 * rw)) ? novel[src] : 0;
+            const bool valid = j < rows && in_range(src, 64 * rw);
+            copy8_or_zero(tile + j * kPad + w, valid ? novel + src : novel, valid);
         }
         copy_async_wait();
         vb.sync();
@@ -70,8 +118,8 @@ __device__ __forceinline__ void encode_body(const VBlock &vb, u64 *tab, u64 *til
             transpose64(A, B, lane);
             const u64 base = (w0 + w) * 64;
             if (in_range(base + 63, 64 * rw)) {
-                f[base + lane] = lin64(tab, A);
-                f[base + lane + 32] = lin64(tab, B);
+                f[base + lane] = lin64_w8(tabs, A);
+                f[base + lane + 32] = lin64_w8(tabs, B);
             }
         }
     }
@@ -97,34 +145,55 @@ __device__ __forceinline__ void encode_small_body(const VBlock &vb, const u64 *G
 }
 
 // ------------------------------------------------------------------- Decode
-// The inverse of Encode: per point, the bits (c_{j n_p + i})_j = h_i R^{-1};
-// a warp transposes the 64 vectors of one word column back into 64 row words.
-__device__ __forceinline__ void decode_body(const VBlock &vb, u64 *tab, u64 *tile, const u64 *GF2X_DATA_RESTRICT h,
-                                            u64 rw, const u64 *__restrict__ dec, u64 *__restrict__ novel, u64 groups,
-                                            u64 stride)
+// The inverse of Encode: per point, the bits (c_{j n_p + i})_j = h_i R^{-1}
+// (four-bit windows through mul_tab: here they measured faster than eight-bit
+// ones); a warp transposes the 64 vectors of one word column back into 64 row
+// words.
+constexpr unsigned kDecodeSmemWords = 16 + kDecodeTabWords + 64 * kPad;
+
+// sm: kDecodeSmemWords words of shared memory (8-byte aligned).
+__device__ __forceinline__ void decode_body(const VBlock &vb, u64 *sm, const u64 *GF2X_DATA_RESTRICT h, u64 rw,
+                                            const u64 *__restrict__ dec, u64 *__restrict__ novel, u64 groups, u64 stride)
 {
+    u64 *tab = align128(sm), *tile = tab + kDecodeTabWords;
+    const unsigned tabs = smem_addr(tab);
     h += (u64)vb.by * stride;
     novel += (u64)vb.by * stride;
-    const int cols = rw < kCols ? (int)rw : kCols;
+    const int cols = rw < kCols ? (int)rw : kCols;   // a power of two
+    const int lc = __ffs(cols) - 1;
     const int lane = vb.t & 31, warp = vb.t >> 5;
     pdl_allow();
-    load_table_async(vb, tab, dec);
+    load_table_async(vb, tab, dec, kDecodeTabWords);
     copy_async_wait();
     vb.sync();
     pdl_wait();
     for (u64 g = vb.bx; g < groups; g += vb.gx) {
         const u64 w0 = g * cols;
-        for (int w = warp; w < cols; w += vb.nt >> 5) {
-            const u64 base = (w0 + w) * 64;
-            const bool ok = in_range(base + 63, 64 * rw);
-            u64 A = ok ? lin64(tab, h[base + lane]) : 0, B = ok ? lin64(tab, h[base + lane + 32]) : 0;
-            transpose64(A, B, lane);
-            tile[lane * kPad + w] = A;
-            tile[(lane + 32) * kPad + w] = B;
+        const int nw = vb.nt >> 5;
+        for (int wb = warp; wb < cols; wb += 4 * nw) {
+            // the loads of up to four columns first, then their products and transposes
+            u64 A[4], B[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = wb + q * nw;
+                const u64 base = (w0 + w) * 64;
+                const bool ok = w < cols && in_range(base + 63, 64 * rw);
+                A[q] = ok ? h[base + lane] : 0;
+                B[q] = ok ? h[base + lane + 32] : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = wb + q * nw;
+                if (w >= cols) break;
+                u64 a = mul_tab(tabs, A[q]), b = mul_tab(tabs, B[q]);
+                transpose64(a, b, lane);
+                tile[lane * kPad + w] = a;
+                tile[(lane + 32) * kPad + w] = b;
+            }
         }
         vb.sync();
         for (int k = vb.t; k < 64 * cols; k += vb.nt) {
-            const int j = k / cols, w = k % cols;
+            const int j = k >> lc, w = k & (cols - 1);
             const u64 dst = (u64)j * rw + w0 + w;
             if (in_range(dst, 64 * rw)) novel[dst] = tile[j * kPad + w];
         }

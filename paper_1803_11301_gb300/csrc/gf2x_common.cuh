@@ -117,6 +117,24 @@ constexpr u64 kM16 = 0x0000FFFF0000FFFFull, kM8 = 0x00FF00FF00FF00FFull, kM4 = 0
 // Lane t holds rows t (A) and t + 32 (B) of a 64x64 bit matrix (bit c of row
 // r = M[r][c]); on return A = column t and B = column t + 32 (bit r = M[r][c]).
 // Applied to columns it returns rows.
+//
+// In the round of distance j, the lane without bit j (L) keeps the low
+// j-bit half of every 2j-bit block and takes its partner's low halves moved
+// up by j; the lane with bit j (H) keeps the high halves and takes the
+// partner's high halves moved down by j.  So every lane keeps (x & keep) and
+// sends its other halves already moved: H rotates them left by j, L right by
+// j (no bit wraps around, since the halves sit at the far side of their
+// blocks); the rotation is two funnel shifts of the 32-bit halves, with the
+// direction a per-lane select, so both kinds of lane run the same code.
+__device__ __forceinline__ u64 transpose_round_send(u64 other, bool up, int j)
+{
+    // rotate right by j (L) or by 64 - j (H: rotate left by j), j <= 16
+    const unsigned lo = (unsigned)other, hi = (unsigned)(other >> 32);
+    const unsigned p = up ? hi : lo, q = up ? lo : hi;
+    const unsigned sh = up ? 32 - j : j;
+    return ((u64)__funnelshift_r(q, p, sh) << 32) | __funnelshift_r(p, q, sh);
+}
+
 __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
 {
     const u64 a2 = (A & 0x00000000FFFFFFFFull) | (B << 32);
@@ -127,15 +145,12 @@ __device__ __forceinline__ void transpose64(u64 &A, u64 &B, int lane)
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int j = 16 >> s;
-        const u64 m = masks[s];
-        const u64 ya = __shfl_xor_sync(0xffffffffu, A, j), yb = __shfl_xor_sync(0xffffffffu, B, j);
-        if (lane & j) {
-            A = ((ya & ~m) >> j) | (A & ~m);
-            B = ((yb & ~m) >> j) | (B & ~m);
-        } else {
-            A = (A & m) | ((ya & m) << j);
-            B = (B & m) | ((yb & m) << j);
-        }
+        const bool up = (lane & j) != 0;
+        const u64 keep = up ? ~masks[s] : masks[s];
+        const u64 ka = A & keep, kb = B & keep;
+        const u64 sa = transpose_round_send(A ^ ka, up, j), sb = transpose_round_send(B ^ kb, up, j);
+        A = ka | __shfl_xor_sync(0xffffffffu, sa, j);
+        B = kb | __shfl_xor_sync(0xffffffffu, sb, j);
     }
 }
 
@@ -329,6 +344,7 @@ struct gf2x_ctx {
     u64 *d_enc;         // 8 x 256: bits (a_{j n_p + i})_j -> f_i  (matrix R)
     u64 *d_dec;         // 8 x 256: f_i -> bits                    (matrix R^{-1})
     u64 *d_cantor;      // v_0 .. v_63
+    u64 *d_dec4;        // 16 x 16: R^{-1} in four-bit windows, mul_tab layout (Decode's shared-memory table)
     int *d_status;      // device status word (gf2x_status)
     GridSync *d_sync;   // barrier state for the stage entry points
     unsigned long long *d_word;   // one device word for measurement checksums (fieldbench.cu)

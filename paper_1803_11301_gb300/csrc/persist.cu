@@ -175,14 +175,14 @@ __device__ __forceinline__ void run_block(const PSeg &S, const VBlock &vb, u64 *
         fftk::store_jobs_body(vb, (const u64 *)A[0], A[1], (const JobDev *)A[2]);
         break;
     case SEG_ENCODE:
-        fftk::encode_body(vb, sm, sm + 8 * 256, (const u64 *)A[0], A[1], S.i[0], (const u64 *)A[2], (u64 *)A[3], A[4],
+        fftk::encode_body(vb, sm, (const u64 *)A[0], A[1], S.i[0], (const u64 *)A[2], (u64 *)A[3], A[4],
                           A[5], A[6]);
         break;
     case SEG_ENCODE_SMALL:
         fftk::encode_small_body(vb, (const u64 *)A[0], S.i[0], A[1], (const u64 *)A[2], (u64 *)A[3], A[4], A[5]);
         break;
     case SEG_DECODE:
-        fftk::decode_body(vb, sm, sm + 8 * 256, (const u64 *)A[0], A[1], (const u64 *)A[2], (u64 *)A[3], A[4], A[5]);
+        fftk::decode_body(vb, sm, (const u64 *)A[0], A[1], (const u64 *)A[2], (u64 *)A[3], A[4], A[5]);
         break;
     case SEG_DECODE_SMALL:
         fftk::decode_small_body(vb, sm, (const u64 *)A[0], S.i[0], (const u64 *)A[1], (u64 *)A[2], A[3]);
