@@ -890,8 +890,11 @@ def run_serving(args, world, rank, local):
             b, key = operand(nb, 3 * k + 1, host)
         return Request(a, na, b, nb, tag=k, host=host, b_key=(key, nb) if args.reuse_frac > 0 else None)
 
+    def drop_output(r):                 # latencies only: a served product is released at once
+        r.out = None
+
     def server():
-        return Server(ctx, streams=3, reuse_after=2 if args.reuse_frac > 0 else 0)
+        return Server(ctx, streams=3, reuse_after=2 if args.reuse_frac > 0 else 0, on_done=drop_output)
 
     srv = server()
     for k in range(min(count, 400)):                        # warm-up
@@ -912,6 +915,7 @@ def run_serving(args, world, rank, local):
         srv.submit(make(k))
     srv.drain()
     sat = count / (time.perf_counter() - t0)
+    del srv
     gaps01 = -np.log(1.0 - synth.uniform01(synth.config_seed(5, 55), count))
 
     def replay(arrivals, submit_fn, poll_fn, done_fn):
@@ -979,6 +983,7 @@ def run_serving(args, world, rank, local):
         s3.submit(make(k, host=True))
     s3.drain()
     sat_e2e = count / (time.perf_counter() - t0)
+    del s3
 
     def served_host(load):
         arrivals = np.cumsum(gaps01 / (load * sat_e2e))

@@ -31,6 +31,13 @@ ones (``Request.host``).  The server then copies its operands to the device on
 the batch's stream before the batch and the product back to a page-locked host
 tensor after it, so a request's latency includes both transfers.
 
+Outputs: a request without a caller-provided ``out`` gets one when a batch
+takes it (device memory, or page-locked host memory for host requests), counted
+against the budget while its batch runs; from then on it belongs to the caller.
+So the memory a server holds is bounded by the batches in flight, however long
+the queue.  ``on_done`` (optional) is called with every completed request, e.g.
+to consume or drop its output.
+
 The library measures launch shapes the first time it meets a shape class,
 which stalls that batch's stream; a server warms up on a representative mix
 and then calls ``Context.tune_freeze()`` so that no request waits on a
@@ -90,7 +97,7 @@ class Server:
     """Admit, batch and complete products; one batch in flight per stream."""
 
     def __init__(self, ctx: Context, streams: int = 3, memory_budget: int | None = None, max_batch: int = 512,
-                 reserve_bytes: int = 2 << 30, reuse_after: int = 0, transform_share: float = 0.25):
+                 reserve_bytes: int = 2 << 30, reuse_after: int = 0, transform_share: float = 0.25, on_done=None):
         import torch
         self.ctx = ctx
         self.device = torch.device("cuda", ctx.device)
@@ -111,6 +118,7 @@ class Server:
         self.transforms: collections.OrderedDict = collections.OrderedDict()
         self.transform_bytes = 0
         self.seen: collections.Counter = collections.Counter()
+        self.on_done = on_done
 
     # ------------------------------------------------------------ requests
     def _request_bytes(self, r: Request) -> int:
@@ -134,11 +142,8 @@ class Server:
             self.rejected.append(req)
             return GF2X_ENOMEM
         nc = product_bits(req.na, req.nb)
-        if req.out is None or req.out.numel() < max(_words(nc), 1):     # else the caller's buffer
-            if req.host:
-                req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64, pin_memory=True)
-            else:
-                req.out = torch.empty(max(_words(nc), 1), dtype=torch.int64, device=self.device)
+        if req.out is not None and req.out.numel() < max(_words(nc), 1):
+            req.out = None                          # too short: the server allocates one at launch
         req.state = "pending"
         self.pending.append(req)
         return GF2X_OK
@@ -212,6 +217,8 @@ class Server:
                     if r.host:                          # the device copies are no longer needed
                         r._dev_a = r._dev_b = r._dev_out = None
                     self.completed.append(r)
+                    if self.on_done is not None:
+                        self.on_done(r)
                 finished += len(bt.reqs)
                 self.in_use -= bt.bytes
                 del self.inflight[k]
@@ -222,8 +229,10 @@ class Server:
             cost = 1024                                 # table alignment and reserved state
             while self.pending and len(take) < self.max_batch:
                 r = self.pending[0]
-                c = self._cost1(r) + (8 * (_words(r.na) + _words(r.nb) + _words(product_bits(r.na, r.nb)))
-                                      if r.host else 0)
+                nw = max(_words(product_bits(r.na, r.nb)), 1)
+                c = self._cost1(r) + (8 * (_words(r.na) + _words(r.nb) + nw) if r.host else 0)
+                if r.out is None and not r.host:
+                    c += 8 * nw                         # the output the server allocates at launch
                 if take and self.in_use + cost + c > self.budget:
                     break
                 take.append(self.pending.popleft())
@@ -231,7 +240,11 @@ class Server:
             if not take:
                 break
             with torch.cuda.stream(st):
-                for r in take:                          # host operands: copies on the batch's stream
+                for r in take:                          # outputs, and host operands' copies on the batch's stream
+                    if r.out is None:
+                        nw = max(_words(product_bits(r.na, r.nb)), 1)
+                        r.out = (torch.empty(nw, dtype=torch.int64, pin_memory=True) if r.host
+                                 else torch.empty(nw, dtype=torch.int64, device=self.device))
                     if r.host:
                         r._dev_a = r.a.to(self.device, non_blocking=True)
                         r._dev_b = r.b.to(self.device, non_blocking=True)

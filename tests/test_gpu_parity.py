@@ -520,6 +520,32 @@ def test_serving_host_operands(ctx):
         assert np.array_equal(got, O.mul(words[0], r.na, words[1], r.nb)), r.tag
 
 
+def test_serving_outputs_allocated_at_launch(ctx):
+    # a queued request holds no output until a batch takes it; on_done sees every
+    # completed request once, with its output in place and equal to the oracle's
+    import torch
+    from paper_1803_11301_gb300.serving import Request, Server
+    done = []
+    srv = Server(ctx, streams=1, max_batch=4, on_done=done.append)
+    words = [synth.operand(synth.config_seed(5, 440 + k), 1 << 16) for k in range(2)]
+    dev = [torch.from_numpy(w.view(np.int64)).cuda() for w in words]
+    lens = synth.loguniform_lengths(synth.config_seed(5, 441), 48, 8.0, 16.0).reshape(24, 2)
+    reqs = []
+    for k, (na, nb) in enumerate(lens):
+        na, nb = int(na), int(nb)
+        r = Request(dev[0][: (na + 63) // 64], na, dev[1][: (nb + 63) // 64], nb, tag=k)
+        reqs.append(r)
+        srv.submit(r)
+    assert all(r.out is None for r in reqs)         # nothing allocated while queued
+    srv.poll()
+    assert sum(r.out is not None for r in reqs) == 4  # the first batch's outputs only
+    srv.drain()
+    torch.cuda.synchronize()
+    assert sorted(r.tag for r in done) == list(range(24))
+    for r in reqs:
+        assert np.array_equal(host_words(r.out, r.na + r.nb - 1), O.mul(words[0], r.na, words[1], r.nb)), r.tag
+
+
 # ------------------------------------------------------------ reused operand
 @pytest.mark.parametrize("na,nb", [(100, 5000), (1 << 16, 1 << 16), (70001, 3333), (1 << 20, 1 << 18), (64, 64)])
 def test_reused_operand_transform(ctx, na, nb):
