@@ -83,7 +83,8 @@ BOTTOM_LAYERS_128 = 10
 # commands).  Each entry carries the digest of the kernel's sources at capture
 # time (comments and blank space stripped, see source_digest): when the
 # sources have changed since, the line reports traffic null and says so.
-KERNEL_SOURCES = {64: ["paper_1803_11301_gb300/csrc/bfly.cu", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"],
+KERNEL_SOURCES = {64: ["paper_1803_11301_gb300/csrc/bfly.cu", "paper_1803_11301_gb300/csrc/bfly_dev.cuh",
+                       "paper_1803_11301_gb300/csrc/gf2x_tables.cuh", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"],
                   128: ["paper_1803_11301_gb300/csrc/m128.cu", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"]}
 TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers): (bytes, source digest)
     ("bottom_fused", 1 << 24, 1 << 24, 64, 9): (8480512 + 0, "3330808bfb1e139a"),

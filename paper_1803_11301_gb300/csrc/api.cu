@@ -541,14 +541,22 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
         // both operands in one launch per stage: a in the lower half of T, b in the upper
         const u64 half = n / 128;
         { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_pair(ctx, a, na, b, nb, T, half, half, st)); }
-        { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, La, false, 2, half, X, st)); }
+        {   // Y (free until Encode) is BasisCvt's side buffer, laid out like X
+            StageScope s(ctx, STAGE_BASISCVT, st);
+            TRY(gf2x::basis_cvt(ctx, T, La, false, 2, half, X, st, Y, half, half));
+        }
         { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, X, La, 2, half, (u64)(Y - X), st)); }
     } else {
         for (int which = 0; which < 2; ++which) {
             u64 *F = which ? Y : X;
             const u64 L = which ? Lb : La;
             { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, which ? b : a, which ? nb : na, T, n / 64, st)); }
-            { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, F, st)); }
+            {   // side buffer: Y for a, the words of T above L for b (Encode reads the first L bits)
+                StageScope s(ctx, STAGE_BASISCVT, st);
+                u64 *side = which ? T + L / 64 : Y;
+                const u64 side_words = which ? n / 64 - L / 64 : buf / 8;
+                TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, F, st, side, 0, side_words));
+            }
             { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, F, L, 1, 0, 0, st)); }
         }
     }
@@ -559,7 +567,10 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
     }
     { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::m128_butterfly_top_inverse(ctx, X, l, 1, 0, st, bt)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::m128_decode(ctx, X, l, T, 1, 0, st)); }
-    { StageScope g(ctx, STAGE_IBASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st)); }
+    {   // X is free once Decode has read it, Y after the pointwise step
+        StageScope g(ctx, STAGE_IBASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st, Y, 0, buf / 8));
+    }
     { StageScope g(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, product_bits(na, nb), c, st)); }
     return GF2X_OK;
 }

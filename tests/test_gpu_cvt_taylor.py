@@ -127,3 +127,14 @@ def test_reused_operand_transform(ctx):
     assert np.array_equal(t2, t1)
     assert np.array_equal(c2, O.mul(a, na, b, nb))
     assert np.array_equal(c1, c2)
+
+
+@pytest.mark.parametrize("na,nb", [(1 << 25, 1 << 25), (1 << 26, (1 << 25) - 3)])
+def test_m128_products_match_the_oracle(ctx, na, nb):
+    # the GF(2^128) path shares BasisCvt: both operands in one call, then one at a time
+    a = synth.operand(rng.getrandbits(63), na)
+    b = synth.operand(rng.getrandbits(63), nb)
+    two_pass, steps = both_forms(ctx, lambda: host(ctx.mul_m128(dev(a), na, dev(b), nb)))
+    want = O.mul(a, na, b, nb)
+    assert np.array_equal(two_pass, want)
+    assert np.array_equal(steps, want)
