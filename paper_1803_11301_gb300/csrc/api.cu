@@ -341,20 +341,28 @@ gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStr
 {
     const int l = log2_u64(r.n) - 6;
     const u64 L = which ? r.Lb : r.La;
-    {
+    // F (the Encode output, free until then) is the scratch buffer of BasisCvt;
+    // its side buffer is Y for a (free until b's forward steps) and, for b, the
+    // words of T above L (Encode reads only the first L bits).  With the
+    // two-pass Taylor part a single product's operand is read in place by
+    // BasisCvt's first kernel, and the load kernel is not needed.
+    const u64 words = buffer_words(r);
+    u64 *side = which ? r.T + L / 64 : r.Y;
+    const u64 side_words = which ? words - L / 64 : words;
+    gf2x::ZetaIO io;
+    const bool direct = !r.jobs && r.count == 1 && gf2x::basis_cvt_two_pass(ctx, L, side_words);
+    if (direct) {
+        io.src[0] = which ? r.b : r.a;
+        io.src_bits[0] = which ? r.nb : r.na;
+    } else {
         StageScope s(ctx, STAGE_LOAD, st);
         if (r.jobs) TRY(gf2x::load_jobs(ctx, r.jobs, which, r.T, r.stride, r.n / 64, r.count, st));
         else TRY(gf2x::load_bits(ctx, which ? r.b : r.a, which ? r.nb : r.na, r.T, r.n / 64, st));
     }
-    // F (the Encode output, free until then) is the scratch buffer of BasisCvt;
-    // its side buffer is Y for a (free until b's forward steps) and, for b, the
-    // words of T above L (Encode reads only the first L bits)
-    const u64 words = buffer_words(r);
-    u64 *side = which ? r.T + L / 64 : r.Y;
-    const u64 side_words = which ? words - L / 64 : words;
     {
         StageScope s(ctx, STAGE_BASISCVT, st);
-        TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st, side, r.stride, side_words));
+        TRY(gf2x::basis_cvt(ctx, r.T, L, false, r.count, r.stride, F, st, side, r.stride, side_words,
+                            direct ? &io : nullptr));
     }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, r.T, l, F, L, r.count, r.stride, r.stride, st)); }
     return GF2X_OK;
@@ -368,13 +376,21 @@ gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
 {
     const int l = log2_u64(r.n) - 6;
     const u64 half = r.n / 128;
-    {
+    // with the two-pass Taylor part BasisCvt's first kernel reads a and b in place
+    gf2x::ZetaIO io;
+    const bool direct = gf2x::basis_cvt_two_pass(ctx, r.La, half);
+    if (direct) {
+        io.src[0] = r.a;
+        io.src[1] = r.b;
+        io.src_bits[0] = r.na;
+        io.src_bits[1] = r.nb;
+    } else {
         StageScope s(ctx, STAGE_LOAD, st);
         TRY(gf2x::load_pair(ctx, r.a, r.na, r.b, r.nb, r.T, half, half, st));
     }
     {   // Y (free until Encode) is the side buffer, laid out like X
         StageScope s(ctx, STAGE_BASISCVT, st);
-        TRY(gf2x::basis_cvt(ctx, r.T, r.La, false, 2, half, r.X, st, r.Y, half, half));
+        TRY(gf2x::basis_cvt(ctx, r.T, r.La, false, 2, half, r.X, st, r.Y, half, half, direct ? &io : nullptr));
     }
     {
         StageScope s(ctx, STAGE_ENCODE, st);
@@ -394,11 +410,19 @@ gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st, int 
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::decode(ctx, r.X, l, r.T, cnt, sd, st)); }
     // X is free once Decode has read it: the scratch buffer of iBasisCvt; Y
     // (free after the pointwise product) its side buffer
-    {
-        StageScope g(ctx, STAGE_IBASISCVT, st);
-        TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st, r.Y, sd, buffer_words(r)));
+    // (with the two-pass Taylor part a single product is written to c by
+    // iBasisCvt's last kernel, and the store kernel is not needed)
+    gf2x::ZetaIO io;
+    const bool direct = !r.jobs && cnt == 1 && gf2x::basis_cvt_two_pass(ctx, r.n, buffer_words(r));
+    if (direct) {
+        io.dst = r.c;
+        io.dst_bits = product_bits(r.na, r.nb);
     }
     {
+        StageScope g(ctx, STAGE_IBASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, r.T, r.n, true, cnt, sd, r.X, st, r.Y, sd, buffer_words(r), direct ? &io : nullptr));
+    }
+    if (!direct) {
         StageScope g(ctx, STAGE_STORE, st);
         if (r.jobs) TRY(gf2x::store_jobs(ctx, r.T, sd, r.jobs, r.max_c_words, cnt, st));
         else TRY(gf2x::store_bits(ctx, r.T, product_bits(r.na, r.nb), r.c, st));
@@ -459,8 +483,19 @@ gf2x_status forward_transform_device(gf2x_ctx *ctx, const u64 *b, u64 nb, u64 n,
     const u64 L = next_pow2(nb) < 64 ? 64 : next_pow2(nb);
     const size_t buf = buffer_bytes(n);
     u64 *X = (u64 *)ws, *Y = (u64 *)((char *)ws + buf), *T = (u64 *)((char *)ws + 2 * buf);
-    { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, b, nb, T, n / 64, st)); }
-    { StageScope s(ctx, STAGE_BASISCVT, st); TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st, Y, 0, buf / 8)); }
+    gf2x::ZetaIO io;
+    const bool direct = gf2x::basis_cvt_two_pass(ctx, L, buf / 8);   // b read in place by BasisCvt
+    if (direct) {
+        io.src[0] = b;
+        io.src_bits[0] = nb;
+    } else {
+        StageScope s(ctx, STAGE_LOAD, st);
+        TRY(gf2x::load_bits(ctx, b, nb, T, n / 64, st));
+    }
+    {
+        StageScope s(ctx, STAGE_BASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, X, st, Y, 0, buf / 8, direct ? &io : nullptr));
+    }
     { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::encode(ctx, T, l, bhat, L, 1, 0, 0, st)); }
     { StageScope s(ctx, STAGE_BUTTERFLY, st); TRY(gf2x::butterfly(ctx, bhat, l, false, 1, 0, st, T)); }
     return GF2X_OK;
@@ -540,22 +575,41 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
     if (La == Lb && 2 * La <= n) {
         // both operands in one launch per stage: a in the lower half of T, b in the upper
         const u64 half = n / 128;
-        { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_pair(ctx, a, na, b, nb, T, half, half, st)); }
+        gf2x::ZetaIO io;                               // a and b read in place by the two-pass BasisCvt
+        const bool direct = gf2x::basis_cvt_two_pass(ctx, La, half);
+        if (direct) {
+            io.src[0] = a;
+            io.src[1] = b;
+            io.src_bits[0] = na;
+            io.src_bits[1] = nb;
+        } else {
+            StageScope s(ctx, STAGE_LOAD, st);
+            TRY(gf2x::load_pair(ctx, a, na, b, nb, T, half, half, st));
+        }
         {   // Y (free until Encode) is BasisCvt's side buffer, laid out like X
             StageScope s(ctx, STAGE_BASISCVT, st);
-            TRY(gf2x::basis_cvt(ctx, T, La, false, 2, half, X, st, Y, half, half));
+            TRY(gf2x::basis_cvt(ctx, T, La, false, 2, half, X, st, Y, half, half, direct ? &io : nullptr));
         }
         { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, X, La, 2, half, (u64)(Y - X), st)); }
     } else {
         for (int which = 0; which < 2; ++which) {
             u64 *F = which ? Y : X;
             const u64 L = which ? Lb : La;
-            { StageScope s(ctx, STAGE_LOAD, st); TRY(gf2x::load_bits(ctx, which ? b : a, which ? nb : na, T, n / 64, st)); }
-            {   // side buffer: Y for a, the words of T above L for b (Encode reads the first L bits)
+            // side buffer: Y for a, the words of T above L for b (Encode reads the first L bits)
+            u64 *side = which ? T + L / 64 : Y;
+            const u64 side_words = which ? n / 64 - L / 64 : buf / 8;
+            gf2x::ZetaIO io;                           // the operand read in place by the two-pass BasisCvt
+            const bool direct = gf2x::basis_cvt_two_pass(ctx, L, side_words);
+            if (direct) {
+                io.src[0] = which ? b : a;
+                io.src_bits[0] = which ? nb : na;
+            } else {
+                StageScope s(ctx, STAGE_LOAD, st);
+                TRY(gf2x::load_bits(ctx, which ? b : a, which ? nb : na, T, n / 64, st));
+            }
+            {
                 StageScope s(ctx, STAGE_BASISCVT, st);
-                u64 *side = which ? T + L / 64 : Y;
-                const u64 side_words = which ? n / 64 - L / 64 : buf / 8;
-                TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, F, st, side, 0, side_words));
+                TRY(gf2x::basis_cvt(ctx, T, L, false, 1, 0, F, st, side, 0, side_words, direct ? &io : nullptr));
             }
             { StageScope s(ctx, STAGE_ENCODE, st); TRY(gf2x::m128_encode(ctx, T, l, F, L, 1, 0, 0, st)); }
         }
@@ -567,11 +621,22 @@ gf2x_status mul128_device(gf2x_ctx *ctx, const u64 *a, u64 na, const u64 *b, u64
     }
     { StageScope g(ctx, STAGE_IBUTTERFLY, st); TRY(gf2x::m128_butterfly_top_inverse(ctx, X, l, 1, 0, st, bt)); }
     { StageScope g(ctx, STAGE_DECODE, st); TRY(gf2x::m128_decode(ctx, X, l, T, 1, 0, st)); }
-    {   // X is free once Decode has read it, Y after the pointwise step
-        StageScope g(ctx, STAGE_IBASISCVT, st);
-        TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st, Y, 0, buf / 8));
+    // X is free once Decode has read it, Y after the pointwise step; with the
+    // two-pass Taylor part iBasisCvt's last kernel writes the product to c
+    gf2x::ZetaIO io;
+    const bool direct = gf2x::basis_cvt_two_pass(ctx, n, buf / 8);
+    if (direct) {
+        io.dst = c;
+        io.dst_bits = product_bits(na, nb);
     }
-    { StageScope g(ctx, STAGE_STORE, st); TRY(gf2x::store_bits(ctx, T, product_bits(na, nb), c, st)); }
+    {
+        StageScope g(ctx, STAGE_IBASISCVT, st);
+        TRY(gf2x::basis_cvt(ctx, T, n, true, 1, 0, X, st, Y, 0, buf / 8, direct ? &io : nullptr));
+    }
+    if (!direct) {
+        StageScope g(ctx, STAGE_STORE, st);
+        TRY(gf2x::store_bits(ctx, T, product_bits(na, nb), c, st));
+    }
     return GF2X_OK;
 }
 

@@ -307,17 +307,24 @@ cudaError_t taylor_window_launch(gf2x_ctx *ctx, u64 *bits, const u64 *src, u64 L
 // the two superset-sum passes of cvt_zeta.cu (bits -> scratch and side ->
 // bits), (b) runs in place on bits, and for m >= 10 the Taylor steps of (b)
 // are the row-level superset sum and carry passes of cvt_zeta.cu.
+// Whether the structured path takes the two-pass Taylor part for 2^(m+16) bits.
+bool two_pass_taylor(gf2x_ctx *ctx, int m, bool has_side, u64 side_words)
+{
+    const u64 need = taylor_zeta_side_words(m);
+    static const int cands[2] = {0, 1};
+    return has_side && need && need <= side_words && !recording(ctx) &&
+           tune_pinned(ctx, TUNE_CVT_TAYLOR, cands, 2, 1) == 1;
+}
+
 cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, int K, bool inverse, int count,
                                  u64 stride, cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0,
-                                 u64 side_words = 0)
+                                 u64 side_words = 0, const ZetaIO *io = nullptr)
 {
     const int m = K - 16;
-    const u64 need = taylor_zeta_side_words(m);
-    if (side && need && need <= side_words && !recording(ctx)) {
-        static const int cands[2] = {0, 1};
-        if (tune_pinned(ctx, TUNE_CVT_TAYLOR, cands, 2, 1) == 1) {
+    if (two_pass_taylor(ctx, m, side != nullptr, side_words)) {
+        {
             if (!inverse) {
-                TRY_CUDA(taylor_zeta(ctx, bits, scratch, side, side_stride, m, false, count, stride, st));
+                TRY_CUDA(taylor_zeta(ctx, bits, scratch, side, side_stride, m, false, count, stride, st, io));
                 if (m <= 9) {
                     TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m, kUnitWordsLog, false, count, stride, st));
                 } else {
@@ -335,9 +342,10 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
                 TRY_CUDA(basis_cvt_outer(ctx, bits, bits, L, m - 8, kUnitWordsLog + 8, true, count, stride, st));
                 TRY_CUDA(outer_taylor_zeta(ctx, bits, side, side_stride, m, true, count, stride, st));
             }
-            return taylor_zeta(ctx, bits, scratch, side, side_stride, m, true, count, stride, st);
+            return taylor_zeta(ctx, bits, scratch, side, side_stride, m, true, count, stride, st, io);
         }
     }
+    if (io && (io->src[0] || io->dst)) return cudaErrorInvalidValue;   // only the two-pass part reads or writes in place
     // Layers in the window kernel (at most 8; the rest are wide steps): its
     // cost grows faster than linearly with the depth (the halo and the rows
     // per block double with each layer), so deep windows pay most while the
@@ -390,13 +398,22 @@ cudaError_t basis_cvt_structured(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 L, 
 
 }  // namespace
 
+bool basis_cvt_two_pass(gf2x_ctx *ctx, u64 L, u64 side_words)
+{
+    int K = 0;
+    while ((1ull << K) < L) ++K;
+    return K >= 18 && K <= 32 && two_pass_taylor(ctx, K - 16, true, side_words);
+}
+
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
-                      cudaStream_t st, u64 *side, u64 side_stride, u64 side_words)
+                      cudaStream_t st, u64 *side, u64 side_stride, u64 side_words, const ZetaIO *io)
 {
     int K = 0;
     while ((1ull << K) < L) ++K;
     if (scratch && K >= 18 && K <= 32)
-        return basis_cvt_structured(ctx, bits, scratch, L, K, inverse, count, stride, st, side, side_stride, side_words);
+        return basis_cvt_structured(ctx, bits, scratch, L, K, inverse, count, stride, st, side, side_stride, side_words,
+                                    io);
+    if (io && (io->src[0] || io->dst)) return cudaErrorInvalidValue;
     std::vector<Step> steps;
     build_steps(K, 1, steps);
     if (scratch && K > 32) {

@@ -72,11 +72,19 @@ __device__ __forceinline__ void superset_sum(u64 *v)
 // skewed columns [c, c + W), W = 256 >> B; the first phase holds 2^A rows of
 // one column in registers, the second (if B > 0) the other 2^B, through
 // shared memory.  src -> dst (main words) and side (overflow words).
-template <int NB>
-__global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_hi(const u64 *__restrict__ src, u64 *__restrict__ dst,
-                                                               u64 *__restrict__ side, u64 stride, u64 side_stride)
+// Operand sources of pass 1 read in place (ZetaIO): job j's words from
+// src[j], words[j] of them, the last one ANDed with mask[j]; zero past them.
+struct HiSrc {
+    const u64 *src0, *src1;
+    u64 words0, words1, mask0, mask1;
+};
+
+template <int NB, bool DIRECT>
+__global__ void __launch_bounds__(kZetaThreads, 3) k_cvt_zeta_hi(const u64 *__restrict__ src, u64 *__restrict__ dst,
+                                                               u64 *__restrict__ side, u64 stride, u64 side_stride,
+                                                               HiSrc ops)
 {
-    constexpr int A = NB < 5 ? NB : 5;
+    constexpr int A = NB < 5 ? NB : NB == 5 ? 4 : 5;   // row bits in registers, first phase
     constexpr int B = NB - A;
     constexpr int J = 1 << NB;
     constexpr int W = kZetaThreads >> B;
@@ -84,7 +92,15 @@ __global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_hi(const u64 *__restr
     extern __shared__ u64 zt[];                       // [J][W] between the phases
     const int u = (int)(blockIdx.x / NWIN);
     const int c = (int)(blockIdx.x % NWIN) * W;
-    src += (u64)blockIdx.y * stride;
+    unsigned nw = 0;                                  // DIRECT: words to read, mask of the last one
+    u64 last = 0;
+    if constexpr (DIRECT) {
+        src = blockIdx.y ? ops.src1 : ops.src0;
+        nw = (unsigned)(blockIdx.y ? ops.words1 : ops.words0);
+        last = blockIdx.y ? ops.mask1 : ops.mask0;
+    } else {
+        src += (u64)blockIdx.y * stride;
+    }
     dst += (u64)blockIdx.y * stride;
     side += (u64)blockIdx.y * side_stride;
     auto store = [&](int j, int w, u64 val) {
@@ -105,9 +121,11 @@ __global__ void __launch_bounds__(kZetaThreads) k_cvt_zeta_hi(const u64 *__restr
             const int j = (s << A) + i;
             const int x = c + w - j;
             const unsigned row = (unsigned)(u + 64 * j);
-            v[i] = (x >= 0 && x < kRowWords && in_range((u64)row * kRowWords + x, (u64)kRowWords << (NB + 6)))
-                       ? src[row * kRowWords + x]
-                       : 0;
+            const unsigned idx = row * kRowWords + x;
+            if constexpr (DIRECT)
+                v[i] = (x >= 0 && x < kRowWords && idx < nw) ? src[idx] & (idx + 1 == nw ? last : ~0ull) : 0;
+            else
+                v[i] = (x >= 0 && x < kRowWords && in_range(idx, (u64)kRowWords << (NB + 6))) ? src[idx] : 0;
         }
         superset_sum<A>(v);
 #pragma unroll
@@ -220,10 +238,13 @@ __device__ __forceinline__ u64 lo_unskew(const u64 *buf, int nld, int u, int o)
 
 // Pass 2: row bits 0..5 and the carries.  Block (group of 64 rows, window c of
 // 32 output words); main (+ side) -> dst.
+// out (null: dst): the product's words written in place of the array's
+// first out_words words (the last one ANDed with out_mask), one job.
 template <bool INV>
 __global__ void __launch_bounds__(kLoThreads) k_cvt_zeta_lo(const u64 *__restrict__ main, const u64 *__restrict__ side,
                                                              u64 *__restrict__ dst, u64 stride, u64 side_stride, int J,
-                                                             unsigned rows)
+                                                             unsigned rows, u64 *__restrict__ out, u64 out_words,
+                                                             u64 out_mask)
 {
     extern __shared__ u64 zs[];
     u64 *buf = zs;                                    // 64 x kLoLoad: loaded, then summed words
@@ -263,16 +284,22 @@ __global__ void __launch_bounds__(kLoThreads) k_cvt_zeta_lo(const u64 *__restric
             val ^= op;
         }
         const unsigned row = row0 + (unsigned)u;
-        if (in_range((u64)row * kRowWords + v, (u64)rows * kRowWords)) dst[row * kRowWords + v] = val;
+        const u64 idx = (u64)row * kRowWords + v;
+        if (out) {
+            if (idx < out_words) out[idx] = idx + 1 == out_words ? val & out_mask : val;
+        } else if (in_range(idx, (u64)rows * kRowWords)) {
+            dst[idx] = val;
+        }
     }
 }
 
 constexpr size_t kLoSmem = (size_t)(64 * (kLoLoad + (kLoW + 1)) + kLoW) * 8;
 
-template <int NB>
-cudaError_t zeta_hi_launch(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st)
+template <int NB, bool DIRECT>
+cudaError_t zeta_hi_run(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st,
+                        const HiSrc &ops)
 {
-    constexpr int A = NB < 5 ? NB : 5;
+    constexpr int A = NB < 5 ? NB : NB == 5 ? 4 : 5;   // row bits in registers, first phase
     constexpr int B = NB - A;
     constexpr int J = 1 << NB;
     constexpr int W = kZetaThreads >> B;
@@ -280,11 +307,20 @@ cudaError_t zeta_hi_launch(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 
     const size_t smem = B > 0 ? (size_t)J * W * 8 : 0;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_cvt_zeta_hi<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem ? smem : 1));
+        cudaFuncSetAttribute(k_cvt_zeta_hi<NB, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem ? smem : 1));
         configured = true;
     }
-    k_cvt_zeta_hi<NB><<<dim3(64 * NWIN, (unsigned)count), kZetaThreads, smem, st>>>(src, dst, side, stride, side_stride);
+    k_cvt_zeta_hi<NB, DIRECT><<<dim3(64 * NWIN, (unsigned)count), kZetaThreads, smem, st>>>(src, dst, side, stride,
+                                                                                           side_stride, ops);
     return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t zeta_hi_launch(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st,
+                           const HiSrc &ops, int direct)
+{
+    return direct ? zeta_hi_run<NB, true>(src, dst, side, stride, side_stride, count, st, ops)
+                  : zeta_hi_run<NB, false>(src, dst, side, stride, side_stride, count, st, ops);
 }
 
 // ------------------------------------------------------ outer Taylor part
@@ -408,18 +444,41 @@ u64 taylor_zeta_side_words(int m) { return m >= 9 && m <= 16 ? 1ull << (2 * m - 
 // (taylor_zeta_side_words(m) words per job, side_stride apart), pass 2 back
 // into bits.
 cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 side_stride, int m, bool inverse,
-                        int count, u64 stride, cudaStream_t st)
+                        int count, u64 stride, cudaStream_t st, const ZetaIO *io)
 {
+    HiSrc ops{};
+    int direct = 0;
+    if (!inverse && io && io->src[0]) {               // the operands read in place (at most two jobs)
+        if (count > 2 || (count == 2 && !io->src[1])) return cudaErrorInvalidValue;
+        auto words = [](u64 bits) { return (bits + 63) / 64; };
+        auto mask = [](u64 bits) { return (bits & 63) ? (~0ull >> (64 - (bits & 63))) : ~0ull; };
+        ops.src0 = io->src[0];
+        ops.words0 = words(io->src_bits[0]);
+        ops.mask0 = mask(io->src_bits[0]);
+        if (count == 2) {
+            ops.src1 = io->src[1];
+            ops.words1 = words(io->src_bits[1]);
+            ops.mask1 = mask(io->src_bits[1]);
+        }
+        direct = 1;
+    }
+    u64 *out = nullptr, out_words = 0, out_mask = ~0ull;
+    if (inverse && io && io->dst) {                    // the product written in place of the array
+        if (count != 1) return cudaErrorInvalidValue;
+        out = io->dst;
+        out_words = (io->dst_bits + 63) / 64;
+        if (io->dst_bits & 63) out_mask = ~0ull >> (64 - (io->dst_bits & 63));
+    }
     cudaError_t e;
     switch (m - 6) {
-    case 3: e = zeta_hi_launch<3>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 4: e = zeta_hi_launch<4>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 5: e = zeta_hi_launch<5>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 6: e = zeta_hi_launch<6>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 7: e = zeta_hi_launch<7>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 8: e = zeta_hi_launch<8>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 9: e = zeta_hi_launch<9>(bits, scratch, side, stride, side_stride, count, st); break;
-    case 10: e = zeta_hi_launch<10>(bits, scratch, side, stride, side_stride, count, st); break;
+    case 3: e = zeta_hi_launch<3>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 4: e = zeta_hi_launch<4>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 5: e = zeta_hi_launch<5>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 6: e = zeta_hi_launch<6>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 7: e = zeta_hi_launch<7>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 8: e = zeta_hi_launch<8>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 9: e = zeta_hi_launch<9>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
+    case 10: e = zeta_hi_launch<10>(bits, scratch, side, stride, side_stride, count, st, ops, direct); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -434,9 +493,11 @@ cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 s
     const dim3 grid((rows / 64) * (kRowWords / kLoW), (unsigned)count);
     const int J = 1 << (m - 6);
     if (inverse)
-        k_cvt_zeta_lo<true><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
+        k_cvt_zeta_lo<true><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows, out,
+                                                               out_words, out_mask);
     else
-        k_cvt_zeta_lo<false><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows);
+        k_cvt_zeta_lo<false><<<grid, kLoThreads, kLoSmem, st>>>(scratch, side, bits, stride, side_stride, J, rows,
+                                                                nullptr, 0, ~0ull);
     count_launch(ctx);
     return cudaGetLastError();
 }

@@ -415,15 +415,31 @@ int tune_stored(gf2x_ctx *ctx, int knob, u64 key, int fallback);
 // `side`, if not null, is a second free buffer of `side_words` words per job,
 // `side_stride` apart: with it (and taylor_zeta_side_words(K - 16) <=
 // side_words), 2^25 <= L <= 2^32 run the Taylor part as two superset-sum passes.
+// Where the two-pass Taylor part reads the array (forward) or writes it
+// (inverse) when that is not `bits`: the operands of a product read in place
+// (job j from src[j], src_bits[j] bits: the last word masked, zeros past it),
+// or the product written to dst (ceil(dst_bits / 64) words, the last one
+// masked; one job).  A null pointer keeps `bits`.
+struct ZetaIO {
+    const u64 *src[2] = {nullptr, nullptr};
+    u64 src_bits[2] = {0, 0};
+    u64 *dst = nullptr;
+    u64 dst_bits = 0;
+};
 cudaError_t basis_cvt(gf2x_ctx *ctx, u64 *bits, u64 L, bool inverse, int count, u64 stride, u64 *scratch,
-                      cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0, u64 side_words = 0);
+                      cudaStream_t st, u64 *side = nullptr, u64 side_stride = 0, u64 side_words = 0,
+                      const ZetaIO *io = nullptr);
+// True when basis_cvt with a scratch buffer and this side buffer runs the
+// two-pass Taylor part for length L: its first kernel then reads ZetaIO's
+// sources (forward) and its last writes ZetaIO's destination (inverse).
+bool basis_cvt_two_pass(gf2x_ctx *ctx, u64 L, u64 side_words);
 // Side-buffer words per job the two-pass Taylor part needs for 2^m rows of
 // 2^16 bits (9 <= m <= 16), else 0.
 u64 taylor_zeta_side_words(int m);
 // The Taylor part of BasisCvt / iBasisCvt of length 2^(m + 16) in two passes
 // (bits -> scratch and side -> bits); cvt_zeta.cu.
 cudaError_t taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *scratch, u64 *side, u64 side_stride, int m, bool inverse,
-                        int count, u64 stride, cudaStream_t st);
+                        int count, u64 stride, cudaStream_t st, const ZetaIO *io = nullptr);
 // The Taylor part of the outer conversion (on rows of 2^16 bits) of the same
 // length, 10 <= m <= 16, in place on bits with the same side buffer.
 cudaError_t outer_taylor_zeta(gf2x_ctx *ctx, u64 *bits, u64 *side, u64 side_stride, int m, bool inverse, int count,
