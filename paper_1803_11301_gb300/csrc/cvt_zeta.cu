@@ -45,7 +45,6 @@ namespace {
 constexpr int kRowWords = 1024;          // tau = 2^16 bits
 constexpr int kZetaThreads = 256;
 constexpr int kLoW = 32;                 // pass 2: output words per block and row
-constexpr int kLoLoad = kLoW + 3;        // widest loaded window (the overflow one)
 constexpr int kLoThreads = (8 * (kLoW + 2) + 31) / 32 * 32;   // a task per (skewed word, row octet) of the widest window
 
 // 8-byte copy global -> shared, or zeros when `valid` is false (no bytes read).
@@ -185,21 +184,48 @@ __device__ __forceinline__ u64 shr_pair(u64 hi, u64 lo, unsigned s)
     return ((u64)__funnelshift_r(l1, h0, r) << 32) | __funnelshift_r(l0, l1, r);
 }
 
+// 16-byte copy global -> shared of `bytes` (16, 8 or 0) bytes, zero-filling the rest.
+__device__ __forceinline__ void copy16_part(u64 *dst_shared, const u64 *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst_shared)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+constexpr int kLoPitch = 36;          // words per row of a pass-2 window: 18 aligned pairs, even for 16-byte copies
+
 // Pass 2 window, first part: P's words [x0 - 1, x0 + NSK) of the 64 rows
-// row0 .. row0+63 into buf (row pitch NSK + 1), each row u skewed by u bits
-// and summed over the row bits 0..5, in place: afterwards buf[u (NSK + 1) + s]
-// holds word x0 + s of x^u gt_u, s < NSK.  One task per (skewed word, row
-// octet): NSK x 8 <= kLoThreads.
-template <int NSK>
+// row0 .. row0+63 into buf, each row u skewed by u bits and summed over the
+// row bits 0..5, in place: afterwards buf[u kLoPitch + s] holds word x0 + s of
+// x^u gt_u, s < NSK.  The words load as 16-byte pairs from the even word
+// xs = x0 - 1 - OFF (OFF = (x0 - 1) & 1): a pair lies in the main words or in
+// the side words (the row boundary 1024 is even), a side pair that crosses the
+// row's degree bound copies its first word and zero-fills the second.  One task
+// per (skewed word, row octet): NSK x 8 <= kLoThreads.
+template <int NSK, int OFF>
 __device__ __forceinline__ void lo_window_sum(const u64 *main, const u64 *side, unsigned row0, int x0, int J,
                                               unsigned rows, u64 *buf)
 {
-    constexpr int NLD = NSK + 1;
-    static_assert(8 * NSK <= kLoThreads, "one task per thread");
-    for (int e = (int)threadIdx.x; e < 64 * NLD; e += kLoThreads) {
-        const int u = e / NLD, k = e - u * NLD;
-        const u64 *p = p_word(main, side, row0 + u, x0 - 1 + k, J, rows);
-        copy8_or_zero(buf + e, p ? p : main, p != nullptr);
+    static_assert(8 * NSK <= kLoThreads && NSK + 1 + OFF <= kLoPitch, "one task per thread, one window per row");
+    constexpr int NPAIR = kLoPitch / 2;
+    const int xs = x0 - 1 - OFF;
+    for (int e = (int)threadIdx.x; e < 64 * NPAIR; e += kLoThreads) {
+        const int u = e / NPAIR, q = e - u * NPAIR;
+        const unsigned row = row0 + (unsigned)u;
+        const int x = xs + 2 * q;                   // even
+        const u64 *p = main;
+        int bytes = 0;
+        if (x >= 0 && row < rows) {
+            if (x < kRowWords) {
+                p = main + row * kRowWords + x;
+                bytes = 16;
+            } else {
+                const int xw = x - kRowWords, lim = J - 1 - (int)(row >> 6);
+                p = side + row * J + xw;
+                bytes = xw + 1 < lim ? 16 : xw < lim ? 8 : 0;
+            }
+        }
+        copy16_part(buf + 2 * e, bytes ? p : main, bytes);
     }
     cvtk::copy_async_wait();
     __syncthreads();
@@ -211,29 +237,23 @@ __device__ __forceinline__ void lo_window_sum(const u64 *main, const u64 *side, 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int u = 8 * a + i;
-            v[i] = shl_pair(buf[u * NLD + sg + 1], buf[u * NLD + sg], (unsigned)u);
+            v[i] = shl_pair(buf[u * kLoPitch + sg + OFF + 1], buf[u * kLoPitch + sg + OFF], (unsigned)u);
         }
         superset_sum<3>(v);
     }
     __syncthreads();                                // every read of the loaded words is done
     if (active)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) buf[(8 * a + i) * NLD + sg] = v[i];
+        for (int i = 0; i < 8; ++i) buf[(8 * a + i) * kLoPitch + sg] = v[i];
     __syncthreads();
     if (active) {                                   // row bits 3..5 (a is now the row's low octet index)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = buf[(a + 8 * i) * NLD + sg];
+        for (int i = 0; i < 8; ++i) v[i] = buf[(a + 8 * i) * kLoPitch + sg];
         superset_sum<3>(v);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) buf[(a + 8 * i) * NLD + sg] = v[i];
+        for (int i = 0; i < 8; ++i) buf[(a + 8 * i) * kLoPitch + sg] = v[i];
     }
     __syncthreads();
-}
-
-// Word o of gt_u from the summed window (pitch nld): unskew by u bits.
-__device__ __forceinline__ u64 lo_unskew(const u64 *buf, int nld, int u, int o)
-{
-    return shr_pair(buf[u * nld + o + 1], buf[u * nld + o], (unsigned)u);
 }
 
 // Pass 2: row bits 0..5 and the carries.  Block (group of 64 rows, window c of
@@ -246,9 +266,9 @@ __global__ void __launch_bounds__(kLoThreads) k_cvt_zeta_lo(const u64 *__restric
                                                              unsigned rows, u64 *__restrict__ out, u64 out_words,
                                                              u64 out_mask)
 {
-    extern __shared__ u64 zs[];
-    u64 *buf = zs;                                    // 64 x kLoLoad: loaded, then summed words
-    u64 *O = buf + 64 * kLoLoad;                      // 64 x (kLoW + 1): overflow words [c - 1, c + kLoW)
+    extern __shared__ __align__(16) u64 zs[];
+    u64 *buf = zs;                                    // 64 x kLoPitch: loaded, then summed words
+    u64 *O = buf + 64 * kLoPitch;                     // 64 x (kLoW + 1): overflow words [c - 1, c + kLoW)
     u64 *prev = O + 64 * (kLoW + 1);                  // kLoW: overflow of the previous group's last row
     constexpr int nwin = kRowWords / kLoW;
     const unsigned grp = blockIdx.x / nwin;
@@ -263,37 +283,45 @@ __global__ void __launch_bounds__(kLoThreads) k_cvt_zeta_lo(const u64 *__restric
             const u64 *p = grp > 0 ? p_word(main, side, row0 - 1, kRowWords + c + (int)threadIdx.x, J, rows) : nullptr;
             prev[threadIdx.x] = p ? *p : 0;
         }
-        lo_window_sum<kLoW + 2>(main, side, row0, kRowWords + c - 1, J, rows, buf);
+        lo_window_sum<kLoW + 2, 0>(main, side, row0, kRowWords + c - 1, J, rows, buf);   // x0 - 1 even
         for (int e = (int)threadIdx.x; e < 64 * (kLoW + 1); e += kLoThreads) {
             const int u = e / (kLoW + 1), o = e - u * (kLoW + 1);
-            O[e] = lo_unskew(buf, kLoW + 3, u, o);
+            O[e] = shr_pair(buf[u * kLoPitch + o + 1], buf[u * kLoPitch + o], (unsigned)u);
         }
         __syncthreads();
     }
-    lo_window_sum<kLoW + 1>(main, side, row0, c, J, rows, buf);
-    for (int e = (int)threadIdx.x; e < 64 * kLoW; e += kLoThreads) {
-        const int u = e / kLoW, o = e - u * kLoW, v = c + o;
-        u64 val = lo_unskew(buf, kLoW + 2, u, o);
+    lo_window_sum<kLoW + 1, 1>(main, side, row0, c, J, rows, buf);                      // x0 - 1 odd
+    // two output words per thread: the summed words o, o+1, o+2 of the row
+    for (int e = (int)threadIdx.x; e < 64 * (kLoW / 2); e += kLoThreads) {
+        const int u = e / (kLoW / 2), o = 2 * (e - u * (kLoW / 2)), v = c + o;
+        const ulonglong2 w01 = *reinterpret_cast<const ulonglong2 *>(buf + u * kLoPitch + o);
+        const u64 w2 = buf[u * kLoPitch + o + 2];
+        u64 g0 = shr_pair(w01.y, w01.x, (unsigned)u), g1 = shr_pair(w2, w01.y, (unsigned)u);
         if (carry) {
-            const u64 op = u ? O[(u - 1) * (kLoW + 1) + o + 1] : prev[o];
+            const u64 *Ou = O + u * (kLoW + 1);
+            const u64 op0 = u ? Ou[o + 1 - (kLoW + 1)] : prev[o];
+            const u64 op1 = u ? Ou[o + 2 - (kLoW + 1)] : prev[o + 1];
             if (!INV) {
-                const u64 ou = O[u * (kLoW + 1) + o + 1];
-                const u64 om = v >= 1 ? O[u * (kLoW + 1) + o] : 0;
-                val ^= (ou << 1) | (om >> 63);
+                const u64 ou0 = Ou[o + 1], ou1 = Ou[o + 2];
+                const u64 om = v >= 1 ? Ou[o] : 0;
+                g0 ^= (ou0 << 1) | (om >> 63);
+                g1 ^= (ou1 << 1) | (ou0 >> 63);
             }
-            val ^= op;
+            g0 ^= op0;
+            g1 ^= op1;
         }
         const unsigned row = row0 + (unsigned)u;
-        const u64 idx = (u64)row * kRowWords + v;
-        if (out) {
-            if (idx < out_words) out[idx] = idx + 1 == out_words ? val & out_mask : val;
-        } else if (in_range(idx, (u64)rows * kRowWords)) {
-            dst[idx] = val;
+        const u64 idx = (u64)row * kRowWords + v;       // even
+        if (out) {                                       // the caller's buffer: 8-byte aligned
+            if (idx < out_words) out[idx] = idx + 1 == out_words ? g0 & out_mask : g0;
+            if (idx + 1 < out_words) out[idx + 1] = idx + 2 == out_words ? g1 & out_mask : g1;
+        } else if (in_range(idx + 1, (u64)rows * kRowWords)) {
+            *reinterpret_cast<ulonglong2 *>(dst + idx) = make_ulonglong2(g0, g1);
         }
     }
 }
 
-constexpr size_t kLoSmem = (size_t)(64 * (kLoLoad + (kLoW + 1)) + kLoW) * 8;
+constexpr size_t kLoSmem = (size_t)(64 * (kLoPitch + (kLoW + 1)) + kLoW) * 8;
 
 template <int NB, bool DIRECT>
 cudaError_t zeta_hi_run(const u64 *src, u64 *dst, u64 *side, u64 stride, u64 side_stride, int count, cudaStream_t st,
