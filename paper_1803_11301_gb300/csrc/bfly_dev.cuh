@@ -48,10 +48,13 @@ constexpr int kBottom = GF2X_BOTTOM_LAYERS;   // bottom tile: 2^11 points (16 Ki
 #endif
 constexpr int kTableMin = GF2X_TABLE_MIN;   // bottom layers >= 4 multiply through tables
 // Layers per top pass (<= 4; compile-time override to measure others).  On
-// GB300, 3 measured 1.6% faster at 2^30-bit operands and even at 2^24; 5 (176
-// to 255 registers, one block per SM) 10% slower.
+// GB300 three-layer passes run at 0.82-0.86 of the table-product peak against
+// 0.75-0.76 for four-layer ones (half the tables per group, half the values per
+// column), which outweighs the extra pass: 9.25 against 9.42 ms per 2^30 x 2^30
+// product, 0.085 against 0.091 ms at 2^22, even at 2^24; 5 layers (176 to 255
+// registers, one block per SM) measured 10% slower.
 #ifndef GF2X_TOP_LAYERS
-#define GF2X_TOP_LAYERS 4
+#define GF2X_TOP_LAYERS 3
 #endif
 constexpr int kTopLayers = GF2X_TOP_LAYERS;
 constexpr int kThreads = 256;
