@@ -87,10 +87,10 @@ KERNEL_SOURCES = {64: ["paper_1803_11301_gb300/csrc/bfly.cu", "paper_1803_11301_
                        "paper_1803_11301_gb300/csrc/gf2x_tables.cuh", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"],
                   128: ["paper_1803_11301_gb300/csrc/m128.cu", "paper_1803_11301_gb300/csrc/gf2x_common.cuh"]}
 TRAFFIC_BYTES_PER_LAUNCH = {     # (stage, na, nb, field bits, bottom layers): (bytes, source digest)
-    ("bottom_fused", 1 << 24, 1 << 24, 64, 11): (8482048 + 0, "9ef7650025a18d4c"),
+    ("bottom_fused", 1 << 24, 1 << 24, 64, 11): (8482048 + 768, "8b7f8352c7915a71"),
     ("bottom_fused", 1 << 24, 1 << 24, 128, 9): (8484096 + 0, "07457971a17da7e1"),
-    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): (537022208 + 224781568, "9ef7650025a18d4c"),
-    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): (537128704 + 224445184, "07457971a17da7e1"),
+    ("bottom_fused", 1 << 30, 1 << 30, 64, 11): (537438208 + 224828928, "8b7f8352c7915a71"),
+    ("bottom_fused", 1 << 30, 1 << 30, 128, 10): (539217408 + 224975360, "07457971a17da7e1"),
 }
 
 

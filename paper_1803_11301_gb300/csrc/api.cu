@@ -336,6 +336,14 @@ struct ClassRun {
 // Words of one job's X, Y or T buffer.
 u64 buffer_words(const ClassRun &r) { return r.count == 1 && r.stride == 0 ? buffer_bytes(r.n) / 8 : r.stride; }
 
+// Set while gf2x_mul_host runs a product on page-locked host memory mapped
+// into the device: its operands and product stay with the load and store
+// kernels (linear streams over the host link) instead of being read and
+// written in place by BasisCvt's first and iBasisCvt's last kernel, whose
+// band-shaped accesses suit device memory.  (Calls on one context are not
+// concurrent, and a cached graph keys on these host pointers.)
+thread_local bool t_mapped_host = false;
+
 // Lines 1-2 (or 4-5) of Alg. 5 for one operand of every job: load, BasisCvt, Encode.
 gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStream_t st)
 {
@@ -350,7 +358,7 @@ gf2x_status forward(gf2x_ctx *ctx, const ClassRun &r, int which, u64 *F, cudaStr
     u64 *side = which ? r.T + L / 64 : r.Y;
     const u64 side_words = which ? words - L / 64 : words;
     gf2x::ZetaIO io;
-    const bool direct = !r.jobs && r.count == 1 && gf2x::basis_cvt_two_pass(ctx, L, side_words);
+    const bool direct = !t_mapped_host && !r.jobs && r.count == 1 && gf2x::basis_cvt_two_pass(ctx, L, side_words);
     if (direct) {
         io.src[0] = which ? r.b : r.a;
         io.src_bits[0] = which ? r.nb : r.na;
@@ -378,7 +386,7 @@ gf2x_status forward_pair(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st)
     const u64 half = r.n / 128;
     // with the two-pass Taylor part BasisCvt's first kernel reads a and b in place
     gf2x::ZetaIO io;
-    const bool direct = gf2x::basis_cvt_two_pass(ctx, r.La, half);
+    const bool direct = !t_mapped_host && gf2x::basis_cvt_two_pass(ctx, r.La, half);
     if (direct) {
         io.src[0] = r.a;
         io.src[1] = r.b;
@@ -413,7 +421,7 @@ gf2x_status inverse_tail(gf2x_ctx *ctx, const ClassRun &r, cudaStream_t st, int 
     // (with the two-pass Taylor part a single product is written to c by
     // iBasisCvt's last kernel, and the store kernel is not needed)
     gf2x::ZetaIO io;
-    const bool direct = !r.jobs && cnt == 1 && gf2x::basis_cvt_two_pass(ctx, r.n, buffer_words(r));
+    const bool direct = !t_mapped_host && !r.jobs && cnt == 1 && gf2x::basis_cvt_two_pass(ctx, r.n, buffer_words(r));
     if (direct) {
         io.dst = r.c;
         io.dst_bits = product_bits(r.na, r.nb);
@@ -1181,7 +1189,9 @@ gf2x_status gf2x_mul_host(gf2x_ctx *ctx, const uint64_t *a_host, uint64_t na, co
                         !overlap(vc, cbytes, va, (size_t)((na + 63) / 64) * 8) &&
                         !overlap(vc, cbytes, vb, (size_t)((nb + 63) / 64) * 8);
     if (direct) {
+        t_mapped_host = true;
         gf2x_status s = op_graph(ctx, OP_MUL, va, na, vb, nb, vc, ws, st);
+        t_mapped_host = false;
         if (s != GF2X_OK) return s;
         TRY(cudaStreamSynchronize(st));
         return GF2X_OK;
