@@ -47,14 +47,6 @@ constexpr int kZetaThreads = 256;
 constexpr int kLoW = 32;                 // pass 2: output words per block and row
 constexpr int kLoThreads = (8 * (kLoW + 2) + 31) / 32 * 32;   // a task per (skewed word, row octet) of the widest window
 
-// 8-byte copy global -> shared, or zeros when `valid` is false (no bytes read).
-__device__ __forceinline__ void copy8_or_zero(u64 *dst_shared, const u64 *src, bool valid)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst_shared)),
-                 "l"(src), "r"(valid ? 8 : 0)
-                 : "memory");
-}
-
 // Superset sum over the N index bits of v[0 .. 2^N): v[i] ^= v[i + 2^t] for
 // every i without bit t.
 template <int N>
@@ -67,17 +59,19 @@ __device__ __forceinline__ void superset_sum(u64 *v)
             if (!(i & (1 << t))) v[i] ^= v[i + (1 << t)];
 }
 
-// Pass 1: row bits 6 .. m-1 (NB = m - 6 of them).  Block (u, window c) over
-// skewed columns [c, c + W), W = 256 >> B; the first phase holds 2^A rows of
-// one column in registers, the second (if B > 0) the other 2^B, through
-// shared memory.  src -> dst (main words) and side (overflow words).
 // Operand sources of pass 1 read in place (ZetaIO): job j's words from
-// src[j], words[j] of them, the last one ANDed with mask[j]; zero past them.
+// src_j, words_j of them, the last one ANDed with mask_j; zero past them.
 struct HiSrc {
     const u64 *src0, *src1;
     u64 words0, words1, mask0, mask1;
 };
 
+// Pass 1: row bits 6 .. m-1 (NB = m - 6 of them).  Block (u, window c) over
+// skewed columns [c, c + W), W = 256 >> B; the first phase holds 2^A rows of
+// one column in registers, the second (if B > 0) the other 2^B, through
+// shared memory.  src (or, DIRECT, the operands of HiSrc) -> dst (main words)
+// and side (overflow words).  At most 85 registers a thread: three blocks per
+// SM keep enough loads in flight for this memory-bound pass.
 template <int NB, bool DIRECT>
 __global__ void __launch_bounds__(kZetaThreads, 3) k_cvt_zeta_hi(const u64 *__restrict__ src, u64 *__restrict__ dst,
                                                                u64 *__restrict__ side, u64 stride, u64 side_stride,
